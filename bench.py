@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: fast SVT (Alg. 6) iterations/s on a 138,000 x 27,000 rating
+matrix with 2e7 entries (1.8e7 observed, 10% held out), plus rSVD-BKI ms at
+2e7 nnz (k = 50, s = 10, p = 3).
+
+A step is one outer SVT iteration (rSVD-BKI or a recycled SVD of the sparse
+iterate, rank decision, shrink, fused evaluation on Phi and update of Y).
+Inputs are synthetic, generated by ``mc_synth.ratings`` (Zipf(1.1) rows and
+columns, half-star values of a rank-20 model plus noise), and stay resident in
+HBM across steps; they exceed L2 (CSR + CSC + values ~ 0.37 GB), so no flush
+is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the float64 CPU
+oracle (the only other implementation of this method here) on the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import mc_synth  # noqa: E402
+
+M_ROWS, N_COLS, N_PAIRS, HOLDOUT, SEED = 138_000, 27_000, 20_000_000, 0.1, 0
+# Step size: 1.2/rho (the usual SVT choice) makes the iteration diverge on this
+# Zipf pattern, whose heaviest rows and columns are fully observed; a constant
+# delta below 2 (the bound under which SVT's fixed-point map contracts) is used.
+DELTA = 1.9
+K_BKI, S_OVER, P_BKI = 50, 10, 3
+HBM_FALLBACK_GBS = 6800.0
+
+
+def workload_config():
+    return {"workload": f"rating-svt {M_ROWS}x{N_COLS} {N_PAIRS:.0e} pairs (10% held out)",
+            "m": M_ROWS, "n": N_COLS, "nnz_observed": int(N_PAIRS * (1 - HOLDOUT)), "nnz_total": N_PAIRS,
+            "tau": "5*sqrt(m*n)", "delta": DELTA, "recycle": "Q (strategy 1), i_reuse=50, q_reuse=10",
+            "p0": 3, "s": S_OVER, "eps": 1e-4, "rsvd_bki": {"k": K_BKI, "s": S_OVER, "p": P_BKI},
+            "l2": "inputs exceed L2 (no flush)", "seed": SEED}
+
+
+def load_workload():
+    """The rating workload, cached under the temp dir (generation takes ~25 s)."""
+    key = hashlib.sha1(f"{M_ROWS},{N_COLS},{N_PAIRS},{HOLDOUT},{SEED},v1".encode()).hexdigest()[:12]
+    path = os.path.join(tempfile.gettempdir(), f"mc_bench_{key}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        o = mc_synth.Observed(M_ROWS, N_COLS, z["row_ptr"], z["col"], z["val"], z["test_rows"], z["test_cols"],
+                              z["test_val"])
+        return o
+    o = mc_synth.ratings(M_ROWS, N_COLS, N_PAIRS, holdout=HOLDOUT, seed=SEED)
+    tmp = path + f".{os.getpid()}.npz"
+    np.savez(tmp, row_ptr=o.row_ptr, col=o.col, val=o.val, test_rows=o.test_rows, test_cols=o.test_cols,
+             test_val=o.test_val)
+    os.replace(tmp, path)
+    return o
+
+
+def full_matrix(o):
+    """All 2e7 pairs (observed + held out) as CSR: the standalone rSVD input."""
+    rows = np.concatenate([o.rows, o.test_rows])
+    cols = np.concatenate([o.col.astype(np.int64), o.test_cols])
+    vals = np.concatenate([o.val, o.test_val])
+    return mc_synth.to_csr(o.m, o.n, rows, cols, vals)
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"mc_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def committed_traffic(kernel_file: str):
+    """Per-launch DRAM bytes of the SpMM from the committed ncu summary, if the
+    kernel source is unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "spmm_dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1810_06860_gb300", "csrc", kernel_file), "rb").read()
+        if d.get("source_sha1") != hashlib.sha1(src).hexdigest():
+            return None
+        return d
+    except (OSError, ValueError):
+        return None
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def svt_params(mc, o):
+    return mc.params(tau=5.0 * math.sqrt(o.m * o.n), delta=DELTA, eps=1e-4, recycle=1, i_reuse=50, q_reuse=10,
+                     seed=SEED)
+
+
+def cpu_oracle_iterations(o, iters: int):
+    """Seconds per SVT iteration of the float64 oracle on the same workload:
+    iterations 2..iters+1 after its own initialisation (callback timestamps)."""
+    from oracle import svt as osvt
+
+    ts = []
+    osvt.svt_fast(o.m, o.n, o.row_ptr, o.col, o.val, tau=5.0 * math.sqrt(o.m * o.n), delta=DELTA, eps=1e-4,
+                  recycle=1, i_reuse=50, q_reuse=10, i_max=iters + 1, seed=SEED,
+                  callback=lambda r: ts.append(time.perf_counter()))
+    d = np.diff(ts)
+    return float(np.sum(d)), len(d)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_1810_06860_gb300 as mc
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mc.load()
+    o = load_workload()
+    stream = torch.cuda.Stream()
+    # ---- rSVD-BKI at 2e7 nnz ------------------------------------------------
+    rp, ci, va = full_matrix(o)
+    hb = mc.Handle(o.m, o.n, rp, ci, va, stream=stream)
+    for i in range(3):
+        hb.rsvd_bki(K_BKI, S_OVER, P_BKI, seed=SEED, call_id=i, device=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nb = 10
+    e0.record(stream)
+    for i in range(nb):
+        hb.rsvd_bki(K_BKI, S_OVER, P_BKI, seed=SEED, call_id=100 + i, device=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bki_ms = e0.elapsed_time(e1) / nb
+    hb.close()
+    del rp, ci, va
+    # ---- SVT iterations -----------------------------------------------------
+    h = mc.Handle(o.m, o.n, o.row_ptr, o.col, o.val, stream=stream)
+    prm = svt_params(mc, o)
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(h.svt_step(prm))
+    torch.cuda.synchronize()
+    h.timing_enable(True)
+    lib = mc.load()
+    l0 = lib.mc_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(h.svt_step(prm))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = lib.mc_launch_count() - l0
+    t_ms = e0.elapsed_time(e1)
+    tm = h.timing_read()
+    h.timing_enable(False)
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = args.steps * world / (t_ms / 1e3)
+    # held-out RMSE of the estimate after the timed iterations
+    pred = h.sample(o.test_rows, o.test_cols)
+    rmse = float(np.sqrt(np.mean((pred.astype(np.float64) - o.test_val) ** 2)))
+    h.close()
+    # ---- roofline of the dominant kernel class (SpMM over CSR + CSC) --------
+    sp_ms = tm["spmm"]["ms"] + tm["spmm_t"]["ms"]
+    sp_bytes = tm["spmm"]["bytes"] + tm["spmm_t"]["bytes"]
+    sp_launch = tm["spmm"]["launches"] + tm["spmm_t"]["launches"]
+    peak, peak_kind = measured_peaks()
+    achieved = (sp_bytes / 1e9) / (sp_ms / 1e3) if sp_ms > 0 else 0.0
+    tr = committed_traffic("k_sparse.cu")
+    roofline = {"bound": "hbm", "kernel": "spmm (Y X over CSR and Y^T X over CSC)", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "algorithmic_bytes_per_launch": sp_bytes / max(sp_launch, 1),
+                "share_of_step": round(sp_ms / t_ms, 3) if t_ms > 0 else None}
+    # ---- end to end through the C ABI with host buffers -----------------------
+    h2d = (o.m + 1) * 8 + o.nnz * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    he = mc.Handle(o.m, o.n, o.row_ptr, o.col, o.val, stream=stream)
+    for _ in range(args.steps):
+        he.svt_step(prm)
+    Us, V, sg = he.factors()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    d2h = Us.nbytes + V.nbytes + sg.nbytes
+    he.close()
+    e2e = {"value": round(args.steps * world / t_e2e, 3), "unit": "iters/s",
+           "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+           "note": "mc_create from host CSR (ingest, CSC build, ||P_Phi M||_2) + K iterations from the start + factors to host"}
+    # ---- CPU oracle baseline (rank 0, N = 1 only) -----------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, its = cpu_oracle_iterations(o, 2)
+        cpu = {"value": round(its / secs, 4), "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"float64 oracle (NumPy/SciPy), SVT iterations 2-{its + 1} of the same workload after its own initialisation"}
+    last = infos[-1]
+    line = {"metric": "SVT iterations/s at 2e7 nnz (rating matrix 138,000 x 27,000)", "value": round(value, 3),
+            "unit": "iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(), parallelism=f"replicas x{world}",
+                           timed_iterations=f"{args.warmup + 1}..{args.warmup + args.steps}",
+                           k_last=last["k"], r_last=last["r"], p_last=last["p"], err_last=round(last["err"], 6),
+                           heldout_rmse=round(rmse, 5)),
+            "rsvd_bki_ms": round(bki_ms, 3), "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "gpu_launches": int(launches),
+            "timing_ms": {k: round(v["ms"], 3) for k, v in tm.items()}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    o = load_workload()
+    from oracle import svt as osvt
+
+    ts = []
+    n_total = args.warmup + args.steps
+    t_start = time.perf_counter()
+    osvt.svt_fast(o.m, o.n, o.row_ptr, o.col, o.val, tau=5.0 * math.sqrt(o.m * o.n), delta=DELTA, eps=1e-4,
+                  recycle=1, i_reuse=50, q_reuse=10, i_max=n_total + 1, seed=SEED,
+                  callback=lambda r: ts.append(time.perf_counter()))
+    d = np.diff(ts)[args.warmup:args.warmup + args.steps]
+    secs = float(np.sum(d))
+    value = len(d) / secs if secs > 0 else 0.0
+    sample = (f"float64 oracle SVT iterations {args.warmup + 2}..{args.warmup + 1 + len(d)} of the same "
+              f"workload on the host cores (first iteration and initialisation untimed)")
+    line = {"impl": "reference", "metric": "SVT iterations/s at 2e7 nnz (rating matrix 138,000 x 27,000)",
+            "value": round(value, 4), "unit": "iters/s", "n_gpus": world, "steps": len(d), "warmup": args.warmup,
+            "ms_per_step": round(1e3 * secs / max(len(d), 1), 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": round(value, 4), "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.perf_counter() - t_start, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 1 or args.steps < 1:
+        ap.error("--steps and --warmup must be >= 1")
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

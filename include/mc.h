@@ -1,0 +1,216 @@
+/*
+ * mc.h -- C ABI of the GB300 fast-SVT matrix-completion library (libmc.so).
+ *
+ * The library computes, on one GPU, the hot path of accelerated singular value
+ * thresholding (Feng, Yu & Li, "Faster Matrix Completion Using Randomized
+ * SVD", arXiv 1810.06860):
+ *   - randomized truncated SVDs of a sparse matrix Y held as CSR plus a CSC
+ *     copy: rSVD-PI (Alg. 4) and rSVD-BKI (Alg. 5), built from eigSVD (Alg. 3);
+ *   - the SVT iteration of Alg. 6 (Sec. IV.C): rank growth, shrink, the update
+ *     Y^i = Y^{i-1} + delta P_Phi(M - X^i) evaluated only on the observed set
+ *     Phi, subspace recycling (Sec. IV.B) and the adaptive power parameter p.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major.  An m x k factor U is U[i*k + j].
+ *   - Singular values are returned in descending order.
+ *   - Pointer arguments marked "host or device" may point to either; the
+ *     library asks the CUDA runtime which one it is.  Output buffers are
+ *     allocated by the caller.
+ *   - Every call returns an mc_status; nothing throws across the ABI.  On
+ *     failure mc_last_error() returns a message for the calling thread.
+ *   - A handle is used by one host thread at a time.  All device work of a
+ *     handle is issued on its stream; calls return after the results they
+ *     report are on the host (they synchronise that stream).
+ *   - Sizes: m, n >= 1, nnz < 2^31 (indices are stored as int32 on the GPU).
+ */
+#ifndef MC_H_
+#define MC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MC_OK = 0,
+  MC_EINVAL = 1,          /* bad argument or input (nothing launched) */
+  MC_ENOMEM = 2,          /* device allocation failed */
+  MC_ECUDA = 3,           /* a CUDA call failed */
+  MC_ENOTCONVERGED = 4,   /* SVT hit i_max; results are still filled */
+  MC_EBUSY = 5,           /* server queue full / job not admitted */
+  MC_PENDING = 6,         /* job not finished yet (mc_poll) */
+  MC_ETIMEOUT = 7,        /* a bounded wait expired */
+  MC_ECANCELLED = 8,      /* job was cancelled */
+  MC_EINTERNAL = 9        /* internal consistency check failed */
+} mc_status;
+
+typedef struct mc_handle_s *mc_handle;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns a device pointer aligned to 256 bytes or NULL; free releases
+ * it.  Both are called on the host thread that calls the library. */
+typedef struct {
+  void *ctx;
+  void *(*alloc)(void *ctx, size_t bytes, void *stream);
+  void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+} mc_allocator;
+
+/* Parameters of Alg. 6 (Sec. IV.C) and of the internal settings of Alg. 2 it
+ * inherits (Sec. II.C).  mc_params_default fills the paper's values. */
+typedef struct {
+  double tau;     /* threshold; <= 0 selects 5*sqrt(m*n) (Sec. II.C's 5n for square) */
+  double delta;   /* step size delta of eq. (6) */
+  double eps;     /* tolerance on ||P_Phi(X - M)||_F / ||P_Phi(M)||_F (Alg. 6 step 16) */
+  int l;          /* rank increment (5) */
+  int s;          /* oversampling (10) */
+  int p0;         /* initial power parameter (3, Alg. 6 step 1) */
+  int p_min;      /* lower bound of p (3) */
+  int p_max;      /* upper bound of p (20) */
+  int i_max;      /* iteration cap (1000) */
+  int i_reuse;    /* first iteration allowed to recycle (50) */
+  int q_reuse;    /* recycled SVD calls per subspace (10) */
+  int recycle;    /* 0 none, 1 reuse Q, 2 reuse U (Sec. IV.B), 3 warm-start Omega with V */
+  int k_max;      /* cap on the SVD rank (0 = min(m,n) - s) */
+  int precision;  /* 0 plain FP32 */
+  uint64_t seed;  /* key of the Philox stream that draws Omega */
+} mc_params;
+
+/* Per-iteration record of mc_svt_step. */
+typedef struct {
+  int i;            /* iteration index (1-based) */
+  int k;            /* rank requested from the last SVD of the repeat loop */
+  int r;            /* r_i = #{sigma_j > tau} */
+  int p;            /* power parameter used */
+  int nsvd;         /* SVD calls in this iteration's repeat loop */
+  int recycled;     /* 1 if any of them recycled a subspace */
+  int converged;    /* 1 if err < eps (Y was not advanced) */
+  int reserved;
+  double err;       /* ||P_Phi(X^i - M)||_F / ||P_Phi(M)||_F */
+  double sigma_last;/* last singular value computed (the repeat test) */
+  double sigma_max; /* largest singular value of Y^{i-1} */
+  double c;         /* c = ceil(tau / (delta ||P_Phi M||_2)) of Y^0 = c delta P_Phi(M) */
+  double norm2;     /* the ||P_Phi(M)||_2 estimate behind c */
+} mc_iter_info;
+
+void mc_params_default(mc_params *p);
+const char *mc_last_error(void);
+/* Number of kernels this library has launched in the process so far. */
+int64_t mc_launch_count(void);
+const char *mc_status_str(mc_status s);
+
+/* mc_create: ingest the observed entries P_Phi(M) (problem (5), Sec. II.C).
+ * row_ptr int64[m+1], col int32[nnz], val float32[nnz] in CSR order; columns
+ * strictly increasing within a row; values finite.  Host or device pointers.
+ * The library copies them into handle-owned device memory and builds the CSC
+ * copy and its permutation.  stream: a cudaStream_t or NULL (the handle
+ * creates its own).  alloc: NULL for cudaMallocAsync on the stream.
+ * Errors: MC_EINVAL for bad shapes, unsorted or duplicate columns, indices out
+ * of range or non-finite values; MC_ENOMEM; MC_ECUDA. */
+mc_status mc_create(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                    const int32_t *col, const float *val, void *stream, const mc_allocator *alloc);
+void mc_destroy(mc_handle h);
+
+/* Set the values of the sparse iterate Y (CSR order, nnz floats, host or
+ * device).  mc_create initialises Y = P_Phi(M). */
+mc_status mc_set_values(mc_handle h, const float *val);
+
+/* mc_rsvd_bki: rank-k truncated SVD of the current Y by rSVD-BKI (Alg. 5):
+ * Gaussian Omega (n x (k+s)) drawn from Philox(seed, call_id); p block-Krylov
+ * steps; B^T = Y^T Q; eigSVD(B^T); the k largest triplets.
+ * (k, p) are clamped so that (p+1)(k+s) <= min(m,n) (k+s itself must fit).
+ * U: m x k_out, S: k_out, V: n x k_out, row-major, host or device; each may be
+ * NULL.  k_out (host) receives the rank returned (k after clamping, fewer if Y
+ * has lower rank).  Buffers must hold k columns. */
+mc_status mc_rsvd_bki(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U,
+                      float *S, float *V, int *k_out);
+
+/* mc_rsvd_pi: as mc_rsvd_bki but by rSVD-PI (Alg. 4): p power steps with a
+ * block normalisation between them, eigSVD of the last block, B^T = Y^T Q. */
+mc_status mc_rsvd_pi(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U,
+                     float *S, float *V, int *k_out);
+
+/* mc_svt_step: one outer iteration of Alg. 6 (steps 3-17).  The first call on
+ * a handle (or the first after mc_svt_reset) also performs step 1: estimates
+ * ||P_Phi(M)||_2, sets c and Y^0 = c delta P_Phi(M).  params is read at that
+ * first call only.  out (host) receives the iteration record.  Returns MC_OK
+ * (also when the tolerance was met: out->converged = 1). */
+mc_status mc_svt_step(mc_handle h, const mc_params *params, mc_iter_info *out);
+mc_status mc_svt_reset(mc_handle h);
+
+/* mc_svt_solve: run mc_svt_step until err < eps or i_max.  Returns MC_OK or
+ * MC_ENOTCONVERGED (results still available).  out (host, may be NULL)
+ * receives the last iteration's record. */
+mc_status mc_svt_solve(mc_handle h, const mc_params *params, mc_iter_info *out);
+
+/* Factors of the current SVT estimate X = Us V^T with Us = U diag(sigma - tau)
+ * (Alg. 6 step 15).  r_out (host) receives r.  Us: m x r, V: n x r, sigma: r
+ * (the singular values before shrinking); host or device; any may be NULL;
+ * buffers must hold max_r columns (MC_EINVAL if r > max_r). */
+mc_status mc_svt_factors(mc_handle h, int max_r, float *Us, float *V, float *sigma, int *r_out);
+
+/* Evaluate the current X at count positions (rows[i], cols[i]) (host or
+ * device int64 arrays) into out (host or device float32). */
+mc_status mc_svt_sample(mc_handle h, int64_t count, const int64_t *rows, const int64_t *cols,
+                        float *out);
+
+/* Values of the current iterate Y in CSR order (nnz floats, host or device). */
+mc_status mc_get_values(mc_handle h, float *val);
+
+/* ---- device timing -------------------------------------------------------
+ * Per kernel class: CUDA-event time on the handle's stream, launches, and the
+ * algorithmic bytes / flops of those launches (compulsory traffic: for a
+ * sparse x panel product 8 nnz + 4 (rows+1) + 4 (rows_in + rows_out) K bytes
+ * and 2 nnz K flops; for the fused update 16 bytes per observed entry plus
+ * the two factor panels).  Off by default; enabling resets the counters. */
+enum {
+  MC_T_SPMM = 0,      /* Y X over CSR */
+  MC_T_SPMM_T = 1,    /* Y^T X over the CSC copy */
+  MC_T_GRAM = 2,      /* X^T X and X^T Y panel products */
+  MC_T_GEMM = 3,      /* panel x small products */
+  MC_T_SMALL = 4,     /* Cholesky / inverse of small Grams */
+  MC_T_EIG = 5,       /* small symmetric eigensolver */
+  MC_T_SDDMM = 6,     /* fused evaluation on Phi + update of Y */
+  MC_T_OTHER = 7,     /* Omega, mirror of Y into CSC order, reductions */
+  MC_T_COUNT = 8
+};
+typedef struct {
+  double ms;
+  double bytes;
+  double flops;
+  int64_t launches;
+} mc_timing;
+mc_status mc_timing_enable(mc_handle h, int on);
+/* out: MC_T_COUNT entries (host).  Synchronises the handle's stream. */
+mc_status mc_timing_read(mc_handle h, mc_timing *out);
+
+/* ---- building blocks, exposed for testing and reuse -------------------- */
+
+/* Omega (n x k) of Alg. 1/4/5 step 1 drawn from Philox4x32-10 with counter
+ * (row, col0 + col, call_lo, call_hi) and key (seed_lo, seed_hi), Box-Muller
+ * z = sqrt(-2 ln u1) cos(2 pi u2), u1 = (x0+1) 2^-32, u2 = x1 2^-32.
+ * out: n x k row-major (host or device).  words (optional, host or device,
+ * uint32 n x k x 2) receives (x0, x1). */
+mc_status mc_omega(int64_t n, int k, uint64_t seed, uint64_t call_id, int col0, float *out,
+                   uint32_t *words);
+
+/* Sparse products with the current Y (L108-113 style products of Alg. 5):
+ * trans = 0: out (m x k) = Y X with X n x k;  trans = 1: out (n x k) = Y^T X
+ * with X m x k.  Row-major, host or device. */
+mc_status mc_spmm(mc_handle h, int trans, int k, const float *X, float *out);
+
+/* Symmetric eigen-decomposition of a dense K x K matrix A (row-major, host or
+ * device; only its lower triangle is read): the kw largest eigenvalues in
+ * descending order into lam (kw floats) and their eigenvectors into W
+ * (K x kw row-major).  The eig() step of eigSVD (Alg. 3).  K <= 1024. */
+mc_status mc_eig_sym(int K, int kw, const float *A, float *lam, float *W);
+
+/* Gram matrix G = X^T X (K x K) of a tall X (R x K row-major), the B = A^T A
+ * step of eigSVD (Alg. 3).  Host or device. */
+mc_status mc_gram(int64_t R, int K, const float *X, float *G);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H_ */

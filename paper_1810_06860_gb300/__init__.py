@@ -1,0 +1,269 @@
+"""GB300 fast-SVT matrix completion (Feng, Yu & Li, arXiv 1810.06860).
+
+Python binding of libmc.so: the same entry points as ``include/mc.h`` with
+argument marshalling only -- every step of the computation runs in the CUDA
+kernels of the library.  Arrays may be NumPy arrays (host) or CUDA torch
+tensors (device); outputs are NumPy arrays unless ``device=True``.
+
+The library needs a CUDA GPU; there is no CPU path.  When torch is available
+its caching allocator is handed to the library as the device allocator.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+from ._native import McIterInfo, McParams
+
+__all__ = ["Handle", "McError", "params", "omega", "eig_sym", "gram", "load", "lib_path"]
+
+load = _native.load
+lib_path = _native.lib_path
+
+
+class McError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(st: int, what: str):
+    if st != _native.MC_OK:
+        lib = load()
+        raise McError(st, f"{what}: {lib.mc_status_str(st).decode()}: {lib.mc_last_error().decode()}")
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, keepalive) for a host NumPy array or a CUDA torch tensor."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return C.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+def _out(shape, dtype, device: bool):
+    if device:
+        import torch
+
+        tdt = {np.float32: torch.float32, np.uint32: torch.int32, np.int64: torch.int64}[dtype]
+        return torch.empty(shape, dtype=tdt, device="cuda")
+    return np.empty(shape, dtype=dtype)
+
+
+def params(**kw) -> McParams:
+    """Alg. 6 parameters with the paper's defaults (mc_params_default)."""
+    p = McParams()
+    load().mc_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _info(i: McIterInfo) -> dict:
+    return {f: getattr(i, f) for f, _ in McIterInfo._fields_ if f != "reserved"}
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through torch's caching allocator."""
+
+    def __init__(self):
+        import torch
+
+        self._torch = torch
+        self.alloc_cb = _native.ALLOC_FN(self._alloc)
+        self.free_cb = _native.FREE_FN(self._free)
+        self.struct = _native.McAllocator(None, self.alloc_cb, self.free_cb)
+
+    def _alloc(self, ctx, nbytes, stream):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(self, ctx, ptr, nbytes, stream):
+        self._torch.cuda.caching_allocator_delete(int(ptr))
+
+
+class Handle:
+    """One completion problem: the observed entries P_Phi(M) in CSR form."""
+
+    def __init__(self, m: int, n: int, row_ptr, col, val, stream=None, torch_alloc: bool = True):
+        lib = load()
+        self._lib = lib
+        self.m, self.n = int(m), int(n)
+        rp, k1 = _ptr(row_ptr, np.int64)
+        ci, k2 = _ptr(col, np.int32)
+        vv, k3 = _ptr(val, np.float32)
+        self.nnz = int(len(col))
+        self._alloc = None
+        alloc_p = None
+        if torch_alloc:
+            try:
+                import torch
+
+                if torch.cuda.is_available():
+                    self._alloc = _TorchAllocator()
+                    alloc_p = C.byref(self._alloc.struct)
+            except ImportError:
+                pass
+        st_ptr = None
+        if stream is not None:
+            st_ptr = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        h = C.c_void_p()
+        _check(lib.mc_create(C.byref(h), self.m, self.n, self.nnz, rp, ci, vv, st_ptr, alloc_p), "mc_create")
+        self._h = h
+
+    @classmethod
+    def from_observed(cls, obs, **kw):
+        return cls(obs.m, obs.n, obs.row_ptr, obs.col, obs.val, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- randomized SVDs -------------------------------------------------
+    def _rsvd(self, fn, k, s, p, seed, call_id, device):
+        U = _out((self.m, k), np.float32, device)
+        S = _out((k,), np.float32, device)
+        V = _out((self.n, k), np.float32, device)
+        ko = C.c_int(0)
+        pu, _ = _ptr(U, np.float32)
+        ps, _ = _ptr(S, np.float32)
+        pv, _ = _ptr(V, np.float32)
+        _check(fn(self._h, k, s, p, seed, call_id, pu, ps, pv, C.byref(ko)), fn.__name__)
+        kk = ko.value
+        return U[:, :kk], S[:kk], V[:, :kk]
+
+    def rsvd_bki(self, k: int, s: int = 10, p: int = 3, seed: int = 0, call_id: int = 0, device: bool = False):
+        """Alg. 5: rank-k SVD (U, S descending, V) of the current iterate."""
+        return self._rsvd(self._lib.mc_rsvd_bki, k, s, p, seed, call_id, device)
+
+    def rsvd_pi(self, k: int, s: int = 10, p: int = 3, seed: int = 0, call_id: int = 0, device: bool = False):
+        """Alg. 4: rank-k SVD of the current iterate by power iteration."""
+        return self._rsvd(self._lib.mc_rsvd_pi, k, s, p, seed, call_id, device)
+
+    # ---- SVT ---------------------------------------------------------------
+    def svt_step(self, prm: McParams | None = None) -> dict:
+        info = McIterInfo()
+        _check(self._lib.mc_svt_step(self._h, C.byref(prm) if prm is not None else None, C.byref(info)),
+               "mc_svt_step")
+        return _info(info)
+
+    def svt_reset(self):
+        _check(self._lib.mc_svt_reset(self._h), "mc_svt_reset")
+
+    def svt_solve(self, prm: McParams) -> dict:
+        info = McIterInfo()
+        st = self._lib.mc_svt_solve(self._h, C.byref(prm), C.byref(info))
+        if st not in (_native.MC_OK, _native.MC_ENOTCONVERGED):
+            _check(st, "mc_svt_solve")
+        return _info(info)
+
+    def factors(self, device: bool = False):
+        r = C.c_int(0)
+        _check(self._lib.mc_svt_factors(self._h, 0, None, None, None, C.byref(r)), "mc_svt_factors")
+        r = r.value
+        Us = _out((self.m, r), np.float32, device)
+        V = _out((self.n, r), np.float32, device)
+        sg = _out((r,), np.float32, device)
+        pu, _ = _ptr(Us, np.float32)
+        pv, _ = _ptr(V, np.float32)
+        ps, _ = _ptr(sg, np.float32)
+        rr = C.c_int(0)
+        _check(self._lib.mc_svt_factors(self._h, r, pu, pv, ps, C.byref(rr)), "mc_svt_factors")
+        return Us, V, sg
+
+    def sample(self, rows, cols, device: bool = False):
+        rows = rows if _is_torch(rows) else np.ascontiguousarray(rows, np.int64)
+        cols = cols if _is_torch(cols) else np.ascontiguousarray(cols, np.int64)
+        out = _out((len(rows),), np.float32, device)
+        pr, _ = _ptr(rows, np.int64)
+        pc, _ = _ptr(cols, np.int64)
+        po, _ = _ptr(out, np.float32)
+        _check(self._lib.mc_svt_sample(self._h, len(rows), pr, pc, po), "mc_svt_sample")
+        return out
+
+    def get_values(self, device: bool = False):
+        out = _out((self.nnz,), np.float32, device)
+        po, _ = _ptr(out, np.float32)
+        _check(self._lib.mc_get_values(self._h, po), "mc_get_values")
+        return out
+
+    def set_values(self, val):
+        pv, keep = _ptr(val, np.float32)
+        _check(self._lib.mc_set_values(self._h, pv), "mc_set_values")
+
+    def timing_enable(self, on: bool = True):
+        _check(self._lib.mc_timing_enable(self._h, 1 if on else 0), "mc_timing_enable")
+
+    def timing_read(self) -> dict:
+        arr = (_native.McTiming * len(_native.TIMING_NAMES))()
+        _check(self._lib.mc_timing_read(self._h, arr), "mc_timing_read")
+        return {name: dict(ms=t.ms, bytes=t.bytes, flops=t.flops, launches=t.launches)
+                for name, t in zip(_native.TIMING_NAMES, arr)}
+
+    def spmm(self, X, trans: bool = False, device: bool = False):
+        """Y X (trans=False, X: n x k) or Y^T X (trans=True, X: m x k)."""
+        k = X.shape[1]
+        out = _out((self.n if trans else self.m, k), np.float32, device)
+        px, keep = _ptr(X, np.float32)
+        po, _ = _ptr(out, np.float32)
+        _check(self._lib.mc_spmm(self._h, 1 if trans else 0, k, px, po), "mc_spmm")
+        return out
+
+
+def omega(n: int, k: int, seed: int, call_id: int = 0, col0: int = 0, words: bool = False):
+    """Philox Gaussian Omega (n x k, float32) and optionally the raw (x0, x1) words."""
+    lib = load()
+    out = np.empty((n, k), np.float32)
+    w = np.empty((n, k, 2), np.uint32) if words else None
+    _check(lib.mc_omega(n, k, seed, call_id, col0, out.ctypes.data_as(C.c_void_p),
+                        w.ctypes.data_as(C.c_void_p) if words else None), "mc_omega")
+    return (out, w) if words else out
+
+
+def eig_sym(A, kw: int):
+    """kw largest eigenpairs (descending) of the symmetric matrix A (float32)."""
+    lib = load()
+    A = np.ascontiguousarray(A, np.float32)
+    K = A.shape[0]
+    lam = np.empty(kw, np.float32)
+    W = np.empty((K, kw), np.float32)
+    _check(lib.mc_eig_sym(K, kw, A.ctypes.data_as(C.c_void_p), lam.ctypes.data_as(C.c_void_p),
+                          W.ctypes.data_as(C.c_void_p)), "mc_eig_sym")
+    return lam, W
+
+
+def gram(X):
+    """X^T X of a tall float32 matrix."""
+    lib = load()
+    X = np.ascontiguousarray(X, np.float32)
+    G = np.empty((X.shape[1], X.shape[1]), np.float32)
+    _check(lib.mc_gram(X.shape[0], X.shape[1], X.ctypes.data_as(C.c_void_p), G.ctypes.data_as(C.c_void_p)),
+           "mc_gram")
+    return G

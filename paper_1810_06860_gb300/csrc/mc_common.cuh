@@ -1,0 +1,162 @@
+// Shared declarations of the GB300 fast-SVT library: error plumbing, device
+// memory, and the host-side launchers of every kernel.  Internal header.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mc.h"
+
+namespace mc {
+
+// ---- errors ---------------------------------------------------------------
+void set_error(const std::string &msg);
+struct Err {
+  mc_status st;
+  std::string msg;
+};
+// Thrown only inside the library; the C ABI catches every Err.
+[[noreturn]] void fail(mc_status st, const std::string &msg);
+
+#define MC_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      ::mc::fail(MC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+// Every kernel launch of the library goes through MC_CHECK_LAUNCH, which also
+// counts it (mc_launch_count).
+void count_launch();
+#define MC_CHECK_LAUNCH()          \
+  do {                             \
+    MC_CUDA(cudaGetLastError());   \
+    ::mc::count_launch();          \
+  } while (0)
+#define MC_REQUIRE(cond, msg)                                                           \
+  do {                                                                                  \
+    if (!(cond)) ::mc::fail(MC_EINVAL, msg);                                            \
+  } while (0)
+
+// ---- device memory ----------------------------------------------------------
+// A growable device buffer owned by a handle; allocation goes through the
+// handle's allocator hook or cudaMallocAsync on its stream.
+struct Alloc {
+  mc_allocator hook{};
+  bool has_hook = false;
+  cudaStream_t stream = nullptr;
+  void *get(size_t bytes);
+  void put(void *p, size_t bytes);
+};
+
+struct DBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  template <class T>
+  T *as() const { return static_cast<T *>(p); }
+  void reserve(Alloc &a, size_t bytes);   // contents not preserved
+  void release(Alloc &a);
+};
+
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---- work decomposition of a compressed sparse matrix -----------------------
+// Rows (or columns, for the CSC copy) are cut into segments of at most SEG
+// entries.  A row with one segment is written directly by the warp that owns
+// it; a longer row writes one partial per segment and a fix-up pass adds them
+// in segment order (deterministic, no atomics).
+constexpr int SEG = 256;
+struct SegPlan {
+  int64_t nseg = 0;      // number of segments (every row has >= 1, empty rows too)
+  int64_t nsplit = 0;    // number of rows with > 1 segment
+  int64_t nslot = 0;     // partial slots (segments of split rows)
+  DBuf seg_row;          // int32[nseg]  row of the segment
+  DBuf seg_beg;          // int32[nseg]  first entry
+  DBuf seg_end;          // int32[nseg]  one past the last entry
+  DBuf seg_slot;         // int32[nseg]  partial slot or -1 (direct write)
+  DBuf split_row;        // int32[nsplit] rows with several segments
+  DBuf split_slot;       // int32[nsplit+1] first slot of each split row
+};
+
+// ---- launchers (k_rng.cu) ---------------------------------------------------
+void launch_omega(cudaStream_t st, int64_t n, int k, int ld, uint64_t seed, uint64_t call_id,
+                  int col0, float *out, uint32_t *words);
+
+// ---- launchers (k_sparse.cu) ------------------------------------------------
+// Build CSC arrays (col_ptr, row_idx, perm: CSC position -> CSR position) from
+// CSR on the device.  tmp must hold >= 4*(n+1) + 4*nnz bytes.
+void build_csc(cudaStream_t st, int64_t m, int64_t n, int64_t nnz, const int *row_ptr,
+               const int *col, int *col_ptr, int *row_idx, int *perm, void *tmp);
+size_t csc_tmp_bytes(int64_t m, int64_t n);
+// int64 row_ptr -> int32 with monotonicity/range checks (flags[0] |= 1 on error)
+void convert_rowptr(cudaStream_t st, int64_t m, int64_t nnz, const int64_t *rp64, int *rp32, int *flags);
+// Validate CSR (sorted unique columns, indices in range, finite values).
+// flags: device int[3] (0 ok); host reads back.
+void validate_csr(cudaStream_t st, int64_t m, int64_t n, const int *row_ptr, const int *col,
+                  const float *val, int *flags);
+void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegPlan &plan);
+// out (rows x K, ld_out) = A (CSR ptr/idx/val) * X (cols x K, ld_x).  K, ld_x,
+// ld_out multiples of 4 (padded columns must be zero in X).  partial must hold
+// plan.nslot * K floats.
+void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, const float *X,
+          int ld_x, int K, float *out, int ld_out, float *partial);
+// y = P_Phi(M) scaled: y[e] = alpha * mval[e]
+void scale_values(cudaStream_t st, int64_t nnz, const float *src, float alpha, float *dst);
+// Yc[p] = Y[perm[p]]
+void mirror_values(cudaStream_t st, int64_t nnz, const int *perm, const float *y, float *yc);
+// Fused SVT update over Phi in CSR order (Alg. 6 steps 15-17):
+//   x_e = <Us[row_e, 0:r], V[col_e, 0:r]>,  res = M_e - x_e,
+//   partial sums of res^2 into seg_sq[nseg] (double),  y_e += delta * res
+//   (only if update != 0).  x_out (optional) receives x_e.
+void sddmm_update(cudaStream_t st, const SegPlan &plan, const int *col, const float *mval, float *y,
+                  const float *Us, int ld_us, const float *V, int ld_v, int r, float delta,
+                  int update, double *seg_sq, float *x_out);
+// Deterministic sum of a double array into out[0] (one block, fixed order).
+void sum_doubles(cudaStream_t st, const double *in, int64_t count, double *out);
+// sum of squares of a float array, deterministic, into out[0] (double).
+void sumsq_floats(cudaStream_t st, const float *in, int64_t count, double *scratch, double *out);
+// Evaluate X = Us V^T at listed positions.
+void sample_lowrank(cudaStream_t st, int64_t count, const int64_t *rows, const int64_t *cols,
+                    const float *Us, int ld_us, const float *V, int ld_v, int r, float *out);
+
+// ---- launchers (k_dense.cu) -------------------------------------------------
+// C (K1 x K2, ld_c) = X^T Y summed over R rows; X (R x K1, ld_x), Y (R x K2,
+// ld_y).  sym: X == Y and only the lower triangle is needed (mirrored).
+// partial: scratch of gemm_tn_scratch_floats(R, K1, K2) floats.
+size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2);
+void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y,
+             int ld_y, float *C, int ld_c, bool sym, float *partial);
+// Z (R x K2, ld_z) = beta * Z + alpha * X (R x K1, ld_x) * W (K1 x K2, ld_w) * diag(colscale)
+// colscale may be NULL (ones).  Z may not alias X.
+void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W,
+             int ld_w, const float *colscale, float alpha, float beta, float *Z, int ld_z);
+// out (K x ncp) = W[:, 0:ncols], zero columns ncols..ncp-1
+void select_cols(cudaStream_t st, int K, const float *W, int ld_w, int ncols, int ncp, float *out);
+// In-place Cholesky of the K x K Gram G (ld) followed by inversion of the
+// factor: Rinv (K x K, ld) = R^{-1} with G + shift I = R^T R.  Pivots <= tiny
+// (zero columns) give an identity row/column so zero columns stay zero.
+// shift_rel: shift = shift_rel * trace(G) / K.  ref_diag (optional, device, K
+// floats): column norms^2 before a projection; columns with G_jj <= ref_tol *
+// ref_diag[j] are treated as absent (dependent on the earlier blocks).
+void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag,
+              float ref_tol, float *Rinv);
+// out[c] = sum_r X[r][c]^2 (deterministic).  scratch: colsumsq_scratch_floats(K).
+size_t colsumsq_scratch_floats(int K);
+void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *out, float *scratch);
+// Top-kw eigenpairs of the symmetric K x K matrix A (lower triangle read).
+// lam: kw floats descending; W: K x kw (ld_w).  work: eig_work_bytes(K, kw).
+size_t eig_work_bytes(int K, int kw);
+void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *lam, float *W, int ld_w,
+              void *work);
+
+}  // namespace mc

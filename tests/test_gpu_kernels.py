@@ -1,0 +1,137 @@
+"""Kernel-level parity of the CUDA library (through the C ABI) against the CPU
+oracle and plain float64 references on the same seeded inputs."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import mc_synth
+from oracle.philox import omega as omega_ref
+from oracle.philox import philox_words
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mc():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_06860_gb300 as mc
+
+    return mc
+
+
+@pytest.mark.parametrize("n,k,seed,call,col0", [(1, 1, 0, 0, 0), (1000, 13, 5, 3, 0), (4097, 64, (7 << 32) | 9, (3 << 32) | 1, 11)])
+def test_omega_words_bit_exact_and_values(mc, n, k, seed, call, col0):
+    z, w = mc.omega(n, k, seed, call, col0, words=True)
+    x0, x1 = philox_words(n, k, seed, call, col0)
+    assert np.array_equal(w[..., 0], x0) and np.array_equal(w[..., 1], x1)
+    ref = omega_ref(n, k, seed, call, col0)
+    assert np.max(np.abs(z - ref) / (1.0 + np.abs(ref))) < 4e-6
+
+
+def _spd(K, spectrum, rng):
+    Qm, _ = np.linalg.qr(rng.standard_normal((K, K)))
+    return (Qm * spectrum) @ Qm.T
+
+
+@pytest.mark.parametrize("K,kw,kind", [(1, 1, "rand"), (2, 2, "rand"), (8, 5, "rand"), (60, 50, "decay"),
+                                        (64, 64, "cluster"), (240, 50, "rating"), (252, 60, "zeros"),
+                                        (300, 80, "decay"), (400, 100, "decay"), (1024, 40, "decay")])
+def test_eig_topk(mc, K, kw, kind):
+    rng = np.random.default_rng(K * 7 + kw)
+    if kind == "rand":
+        B = rng.standard_normal((K, K))
+        A = B @ B.T
+    elif kind == "decay":
+        A = _spd(K, 1e4 * 0.97 ** np.arange(K), rng)
+    elif kind == "cluster":
+        s = np.repeat([100.0, 50.0, 49.9999, 10.0], K // 4)
+        A = _spd(K, s, rng)
+    elif kind == "rating":
+        s = np.concatenate([[5e5], np.linspace(8000, 6000, 60), np.linspace(6000, 100, K - 61)])
+        A = _spd(K, s, rng)
+    else:  # zero rows/columns from padding
+        A = _spd(K, np.concatenate([np.linspace(1e3, 1, K - 12), np.zeros(12)]), rng)
+        P = np.eye(K)[rng.permutation(K)]
+        A = P @ A @ P.T
+        A[:, :12] = 0
+        A[:12, :] = 0
+    A = A.astype(np.float32)
+    lam, W = mc.eig_sym(A, kw)
+    A64 = A.astype(np.float64)
+    ref = np.linalg.eigvalsh(A64)[::-1][:kw]
+    scale = max(abs(ref[0]), 1e-30)
+    assert np.max(np.abs(lam - ref)) <= 2e-5 * scale * max(1.0, np.sqrt(K) / 8)
+    W64 = W.astype(np.float64)
+    assert np.max(np.abs(W64.T @ W64 - np.eye(kw))) < 1e-4
+    res = np.linalg.norm(A64 @ W64 - W64 * lam.astype(np.float64), axis=0)
+    assert np.max(res) <= 1e-4 * scale * max(1.0, np.sqrt(K) / 8)
+
+
+@pytest.mark.parametrize("R,K", [(1, 1), (37, 5), (1000, 60), (5000, 64), (20000, 100), (3000, 256), (1200, 300)])
+def test_gram(mc, R, K):
+    rng = np.random.default_rng(R + K)
+    X = rng.standard_normal((R, K)).astype(np.float32)
+    G = mc.gram(X)
+    ref = X.astype(np.float64).T @ X.astype(np.float64)
+    assert np.max(np.abs(G - ref)) <= 1e-5 * np.max(np.abs(ref)) * max(1, np.sqrt(R / 1000))
+
+
+def _rand_csr(m, n, density, rng, heavy_row=None, heavy_col=None):
+    A = sp.random(m, n, density=density, random_state=np.random.RandomState(rng.integers(1 << 30)), format="lil")
+    if heavy_row is not None:
+        A[heavy_row, :] = rng.standard_normal(n)
+    if heavy_col is not None:
+        A[:, heavy_col] = rng.standard_normal((m, 1))
+    A = A.tocsr()
+    A.sort_indices()
+    A.data = rng.standard_normal(A.nnz).astype(np.float32)
+    return A
+
+
+@pytest.mark.parametrize("K", [1, 3, 4, 8, 60, 64, 100, 128, 240, 300, 1024])
+def test_spmm_both_ways(mc, K):
+    rng = np.random.default_rng(K)
+    m, n = 700, 900
+    A = _rand_csr(m, n, 0.01, rng, heavy_row=5, heavy_col=17)  # rows/cols longer than one segment
+    A[10:20, :] = 0  # empty rows
+    A.eliminate_zeros()
+    A.sort_indices()
+    with mc.Handle(m, n, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float32)) as h:
+        X = rng.standard_normal((n, K)).astype(np.float32)
+        Xt = rng.standard_normal((m, K)).astype(np.float32)
+        A64 = A.astype(np.float64)
+        Y1 = h.spmm(X)
+        Y2 = h.spmm(Xt, trans=True)
+        r1 = A64 @ X.astype(np.float64)
+        r2 = A64.T @ Xt.astype(np.float64)
+        assert np.max(np.abs(Y1 - r1)) < 1e-4 * max(1, np.abs(r1).max())
+        assert np.max(np.abs(Y2 - r2)) < 1e-4 * max(1, np.abs(r2).max())
+        # deterministic
+        assert np.array_equal(Y1, h.spmm(X))
+
+
+def test_create_rejects_bad_input(mc):
+    rp = np.array([0, 2, 3], np.int64)
+    with pytest.raises(mc.McError) as e:
+        mc.Handle(2, 4, rp, np.array([1, 1, 0], np.int32), np.ones(3, np.float32))
+    assert e.value.status == 1
+    with pytest.raises(mc.McError):
+        mc.Handle(2, 4, rp, np.array([0, 5, 0], np.int32), np.ones(3, np.float32))
+    with pytest.raises(mc.McError):
+        mc.Handle(2, 4, rp, np.array([0, 1, 0], np.int32), np.array([1, np.nan, 1], np.float32))
+    with pytest.raises(mc.McError):
+        mc.Handle(2, 4, np.array([0, 3, 2], np.int64), np.array([0, 1, 0], np.int32), np.ones(3, np.float32))
+    with pytest.raises(mc.McError):
+        mc.Handle(0, 4, np.array([0], np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+
+
+def test_csc_copy_matches_transpose(mc):
+    o = mc_synth.ratings(m=3000, n=800, N=60000, seed=1)
+    with mc.Handle.from_observed(o) as h:
+        rng = np.random.default_rng(0)
+        Xt = rng.standard_normal((o.m, 8)).astype(np.float32)
+        A = sp.csr_matrix((o.val.astype(np.float64), o.col, o.row_ptr), shape=(o.m, o.n))
+        got = h.spmm(Xt, trans=True)
+        assert np.max(np.abs(got - A.T @ Xt.astype(np.float64))) < 1e-4 * np.abs(got).max()
