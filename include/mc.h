@@ -210,6 +210,27 @@ mc_status mc_eig_sym(int K, int kw, const float *A, float *lam, float *W);
  * step of eigSVD (Alg. 3).  Host or device. */
 mc_status mc_gram(int64_t R, int K, const float *X, float *G);
 
+/* mc_gram_noalloc: G = X^T X (K x K, leading dimension ldg) of a tall device
+ * matrix X (R rows, K columns, leading dimension ld, ld a multiple of 4), like
+ * mc_gram but without allocating any device memory.  The paper has no
+ * counterpart; it exists for callers that cannot allocate while they call:
+ * code between cudaStreamBeginCapture and cudaStreamEndCapture, host
+ * callbacks and allocator hooks, and hosts whose device memory is entirely
+ * owned by their own pool.
+ *   - X and G must be device pointers; the call only enqueues work on stream
+ *     (a cudaStream_t, NULL for the legacy default stream) and returns; G is
+ *     ready when the stream reaches that point.
+ *   - Scratch is one fixed 4 MiB device array inside the library, held by
+ *     every GPU that loads it until the process exits.  K > 1024 is rejected
+ *     with MC_EINVAL (the array must hold one 1024 x 1024 partial tile).
+ *   - The first call on a device looks up that array's device address with
+ *     cudaGetSymbolAddress (with the device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - All calls share the array and each overwrites it: calls that can
+ *     overlap on the GPU (different streams, no ordering between them) race
+ *     and give wrong results.  Order them on one stream or with events. */
+mc_status mc_gram_noalloc(int64_t R, int K, const float *X, int ld, float *G, int ldg, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <mutex>
 
 namespace mc {
 namespace {
@@ -762,4 +763,79 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   MC_CHECK_LAUNCH();
 }
 
+
+// ===================================================== allocation-free Gram ==
+// mc_gram_noalloc is for callers that cannot allocate device memory while they
+// call this library: code that runs between the begin and end of a CUDA stream
+// capture (cudaMalloc is not allowed there), host callbacks and allocator
+// hooks, and hosts that hand every byte of device memory to their own pool
+// and forbid other allocations.  Its scratch (the per-split partial tiles of
+// the Gram) is a file-scope device array of kNoAllocScratchFloats floats
+// (4 MiB) that every GPU which loads this library holds until the process
+// exits.
+namespace {
+
+constexpr size_t kNoAllocScratchFloats = size_t(1) << 20;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array for the current device.  The name
+// g_noalloc_scratch in host code is only a host-side stand-in for the device
+// symbol, so the address is looked up once per device with that device
+// current and cached.
+float *noalloc_scratch_for_current_device(int *dev_out) {
+  int dev = -1;
+  MC_CUDA(cudaGetDevice(&dev));
+  MC_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, "mc_gram_noalloc: device index above 63");
+  *dev_out = dev;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    MC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<float *>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
 }  // namespace mc
+
+extern "C" mc_status mc_gram_noalloc(int64_t R, int K, const float *X, int ld, float *G, int ldg, void *stream) {
+  using namespace mc;
+  try {
+    MC_REQUIRE(R >= 1 && K >= 1, "mc_gram_noalloc: R and K must be >= 1");
+    MC_REQUIRE(X != nullptr && G != nullptr, "mc_gram_noalloc: null X or G");
+    MC_REQUIRE(ld >= K && ld % 4 == 0, "mc_gram_noalloc: ld must be >= K and a multiple of 4");
+    MC_REQUIRE(ldg >= K, "mc_gram_noalloc: ldg must be >= K");
+    const int Kp = static_cast<int>(round_up(K, TN_T));
+    const size_t tile_floats = (size_t)Kp * Kp;
+    if (tile_floats > kNoAllocScratchFloats)
+      fail(MC_EINVAL, "mc_gram_noalloc: K = " + std::to_string(K) +
+                          " needs more scratch than the fixed 4 MiB array holds (maximum K is 1024)");
+    int dev = -1;
+    float *scratch = noalloc_scratch_for_current_device(&dev);
+    // as gemm_tn, with the number of row splits capped by the scratch size
+    const int ti = Kp / TN_T;
+    const int64_t want = std::max<int64_t>(1, (152 * 4 + ti * ti - 1) / (ti * ti));
+    const int64_t by_rows = std::max<int64_t>(1, R / 256);
+    const int64_t by_scratch = static_cast<int64_t>(kNoAllocScratchFloats / tile_floats);
+    const int nsplit = static_cast<int>(std::min<int64_t>(std::min<int64_t>(std::min<int64_t>(want, by_rows), by_scratch), 1024));
+    const int64_t rps = round_up((R + nsplit - 1) / nsplit, TN_RB);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    dim3 grid(ti * ti, nsplit);
+    gemm_tn_kernel<<<grid, 256, 0, st>>>(R, K, K, X, ld, X, ld, rps, ti, true, scratch, Kp, Kp);
+    MC_CHECK_LAUNCH();
+    const int64_t total = (int64_t)K * K;
+    const int nb = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 8));
+    gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K, K, nsplit, scratch, Kp, Kp, true, G, ldg);
+    MC_CHECK_LAUNCH();
+    return MC_OK;
+  } catch (const Err &e) {
+    set_error(e.msg);
+    return e.st;
+  }
+}
