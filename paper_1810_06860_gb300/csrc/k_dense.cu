@@ -5,7 +5,6 @@
 //             Ritz vectors U = Q W of Alg. 5 step 11, H R^-1)
 //   chol_inv  R^-1 of the Cholesky factor of a small Gram (block normalisation
 //             standing in for lu() and orth(), which Lemmas 2-3 allow)
-//   eig_topk  leading eigenpairs of a small symmetric matrix (Alg. 3 step 2)
 // All float32; every reduction runs in a fixed order (deterministic).
 #include "mc_common.cuh"
 
@@ -69,19 +68,39 @@ gemm_tn_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x,
   }
 }
 
-__global__ void gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ partial, int K1p,
-                                      int K2p, bool sym, float *__restrict__ C, int ld_c) {
+// Sum of the per-split partial tiles, in split order: a block covers 32
+// outputs with 8 lanes of split groups each, then adds the 8 group sums in order.
+__global__ void __launch_bounds__(256)
+gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ partial, int K1p, int K2p, bool sym,
+                      float *__restrict__ C, int ld_c) {
+  __shared__ float sh[8][33];
   const int64_t total = (int64_t)K1 * K2;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    int i = static_cast<int>(t / K2), j = static_cast<int>(t % K2);
-    int si = i, sj = j;
-    if (sym && (j / TN_T) < (i / TN_T)) {  // tile below the diagonal: read the mirrored tile
-      si = j;
-      sj = i;
-    }
+  const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int64_t tile = (int64_t)K1p * K2p;
+  for (int64_t base = (int64_t)blockIdx.x * 32; base < total; base += (int64_t)gridDim.x * 32) {
+    const int64_t t = base + o;
     float acc = 0.f;
-    for (int s = 0; s < nsplit; ++s) acc += partial[(int64_t)s * K1p * K2p + (int64_t)si * K2p + sj];
-    C[(int64_t)i * ld_c + j] = acc;
+    int i = 0, j = 0;
+    if (t < total) {
+      i = static_cast<int>(t / K2);
+      j = static_cast<int>(t % K2);
+      int si = i, sj = j;
+      if (sym && (j / TN_T) < (i / TN_T)) {  // tile below the diagonal: read the mirrored tile
+        si = j;
+        sj = i;
+      }
+      const float *src = partial + (int64_t)si * K2p + sj;
+      for (int sp = g; sp < nsplit; sp += 8) acc += src[sp * tile];
+    }
+    sh[g][o] = acc;
+    __syncthreads();
+    if (g == 0 && t < total) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += sh[q][o];
+      C[(int64_t)i * ld_c + j] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -155,35 +174,44 @@ gemm_nn_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x,
 }
 
 // =========================================================== chol_inv ======
-// One block.  G + shift I = L L^T (right-looking), pivots below the drop
-// threshold make their column "absent": its row of L^{-1} is zero, so the
-// matching column of H R^{-1} is zero and the others ignore it.
+// One block.  G + shift I = L L^T (right-looking, warp per row of the trailing
+// update); pivots below the drop threshold make their column "absent": its
+// row of L^{-1} is zero, so the matching column of H R^{-1} is zero and the
+// others ignore it.  L^{-1} by forward substitution, one thread per column,
+// reading L as warp broadcasts; the result is written transposed: R^{-1}.
 __global__ void __launch_bounds__(1024)
 chol_inv_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
-                float ref_tol, float *__restrict__ Rinv, float *__restrict__ gwork) {
+                float ref_tol, float *__restrict__ Rinv, int X_in_smem) {
   extern __shared__ float sh[];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const bool in_smem = gwork == nullptr;
-  float *L = in_smem ? sh : gwork;  // K x K (lower), then L^{-1}
-  float *flags = in_smem ? sh + (size_t)K * K : sh;  // K floats: 1 = kept
+  const int wid = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  float *L = sh;                                   // K x K, lower
+  float *flags = sh + (size_t)K * K;               // K: 1 = kept
+  float *X = X_in_smem ? flags + K : Rinv;         // K x K: L^{-1} (X[l][c])
   __shared__ float s_tr, s_max;
-  if (tid == 0) {
+  if (tid < 32) {
     float tr = 0.f, mx = 0.f;
-    for (int i = 0; i < K; ++i) {
-      tr += G[(int64_t)i * ld + i];
-      mx = fmaxf(mx, G[(int64_t)i * ld + i]);
+    for (int i = lane; i < K; i += 32) {
+      const float gi = G[(int64_t)i * ld + i];
+      tr += gi;
+      mx = fmaxf(mx, gi);
     }
-    s_tr = tr;
-    s_max = mx;
+    for (int off = 16; off > 0; off >>= 1) {
+      tr += __shfl_xor_sync(0xffffffffu, tr, off);
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if (lane == 0) {
+      s_tr = tr;
+      s_max = mx;
+    }
   }
-  __syncthreads();
-  const float shift = shift_rel * s_tr / K;
-  const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
   // a column that lost (almost) all of its norm to an earlier projection is
   // rounding noise: remove it before factoring
   for (int i = tid; i < K; i += nt)
     flags[i] = (ref_diag && !(G[(int64_t)i * ld + i] > ref_tol * ref_diag[i])) ? 0.f : 1.f;
   __syncthreads();
+  const float shift = shift_rel * s_tr / K;
+  const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
   for (int t = tid; t < K * K; t += nt) {
     const int i = t / K, j = t % K;
     const bool live = flags[i] != 0.f && flags[j] != 0.f;
@@ -193,442 +221,50 @@ chol_inv_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, con
   for (int j = 0; j < K; ++j) {
     const float d = L[j * K + j];
     const bool keep = d > drop;
+    const float inv = keep ? rsqrtf(d) : 0.f;
     __syncthreads();  // every thread has read the pivot before it is overwritten
-    // column j
-    if (keep) {
-      const float ljj = sqrtf(d), inv = 1.0f / ljj;
-      for (int i = j + 1 + tid; i < K; i += nt) L[i * K + j] *= inv;
-      if (tid == 0) L[j * K + j] = ljj;
-    } else {
-      for (int i = j + 1 + tid; i < K; i += nt) L[i * K + j] = 0.f;
-      if (tid == 0) L[j * K + j] = 1.0f;
-    }
-    __syncthreads();
-    if (tid == 0) flags[j] = keep ? 1.f : 0.f;
-    __syncthreads();
-    if (keep) {
-      // trailing update of the lower triangle: L[a][b] -= L[a][j] L[b][j], j < b <= a
-      const int n = K - j - 1;
-      const int64_t tot = (int64_t)n * (n + 1) / 2;
-      for (int64_t f = tid; f < tot; f += nt) {
-        int a = static_cast<int>((sqrtf(8.0f * f + 1.0f) - 1.0f) * 0.5f);
-        while ((int64_t)(a + 1) * (a + 2) / 2 <= f) ++a;
-        while ((int64_t)a * (a + 1) / 2 > f) --a;
-        const int b = static_cast<int>(f - (int64_t)a * (a + 1) / 2);
-        const int ga = j + 1 + a, gb = j + 1 + b;
-        L[ga * K + gb] -= L[ga * K + j] * L[gb * K + j];
-      }
-    }
-    __syncthreads();
-  }
-  // L^{-1} by columns: thread c solves L x = e_c (forward substitution).
-  // Written to the strictly upper part as scratch, then transposed out.
-  for (int c = tid; c < K; c += nt) {
-    // x_i for i >= c stored in Rinv column c temporarily (global), row-major Rinv[i][c]
-    for (int i = 0; i < K; ++i) Rinv[(int64_t)i * K + c] = 0.f;
-    if (flags[c] == 0.f) continue;
-    for (int i = c; i < K; ++i) {
-      if (flags[i] == 0.f) continue;
-      float acc = (i == c) ? 1.0f : 0.0f;
-      for (int l = c; l < i; ++l) acc -= L[i * K + l] * Rinv[(int64_t)l * K + c];
-      Rinv[(int64_t)i * K + c] = acc / L[i * K + i];
-    }
-  }
-  __syncthreads();
-  // Rinv currently holds L^{-1} (row-major).  R^{-1} = (L^{-1})^T: transpose in place.
-  for (int t = tid; t < K * K; t += nt) {
-    const int i = t / K, j = t % K;
-    if (i < j) {
-      const float a = Rinv[(int64_t)i * K + j], b = Rinv[(int64_t)j * K + i];
-      Rinv[(int64_t)i * K + j] = b;
-      Rinv[(int64_t)j * K + i] = a;
-    }
-  }
-}
-
-// =========================================================== eig_topk ======
-// One block of 1024 threads.
-//  1. Householder reduction of the symmetric matrix (packed lower triangle)
-//     to tridiagonal form T = Q^T A Q.
-//  2. Sturm-count multisection for the kw largest eigenvalues of T.
-//  3. Inverse iteration (partially pivoted tridiagonal LU, three solves from
-//     a fixed pseudo-random start) for their eigenvectors.
-//  4. Classical Gram-Schmidt, applied twice, in descending-eigenvalue order.
-//  5. Back-transformation W = Q Z by the stored reflectors.
-constexpr int EIG_THREADS = 1024;
-constexpr size_t EIG_SMEM = 220 * 1024;
-
-__device__ __forceinline__ int64_t pk(int r, int c) { return (int64_t)r * (r + 1) / 2 + c; }  // r >= c
-
-__device__ float block_sum(float v, float *red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  float t = 0.f;
-  if (threadIdx.x < 32) {
-    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    if (threadIdx.x == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
-
-__device__ __forceinline__ uint32_t hash32(uint32_t x) {
-  x ^= x >> 16;
-  x *= 0x7feb352du;
-  x ^= x >> 15;
-  x *= 0x846ca68bu;
-  x ^= x >> 16;
-  return x;
-}
-
-__global__ void __launch_bounds__(EIG_THREADS, 1)
-eig_topk_kernel(int K, int kw, const float *__restrict__ A, int lda, float *__restrict__ lam_out,
-                float *__restrict__ W, int ld_w, float *__restrict__ gw, int P_in_smem, int Z_in_smem) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ float red[40];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  // --- layout ---
-  float *d = sm;                 // K
-  float *e = d + K;              // K
-  float *beta = e + K;           // K
-  float *v = beta + K;           // K
-  float *pw = v + K;             // K
-  float *lam = pw + K;           // kw
-  float *lo = lam + kw;          // kw
-  float *hi = lo + kw;           // kw
-  float *hvec = hi + kw;         // kw
-  float *base = hvec + kw;
-  base = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(base) + 15) & ~uintptr_t(15));
-  const int64_t npk = (int64_t)K * (K + 1) / 2;
-  float *P = P_in_smem ? base : gw;
-  float *gnext = P_in_smem ? gw : gw + round_up(npk, 64);
-  float *Z;
-  if (Z_in_smem) {
-    Z = P_in_smem ? base + round_up(npk, 4) : base;
-  } else {
-    Z = gnext;
-    gnext += round_up((int64_t)K * kw, 64);
-  }
-  float *fa = gnext;                      // inverse-iteration factors, [i * kw + t]
-  float *fb = fa + (int64_t)K * kw;
-  float *fc = fb + (int64_t)K * kw;
-  float *fl = fc + (int64_t)K * kw;
-  float *fp = fl + (int64_t)K * kw;
-
-  // ---- load the lower triangle ----
-  for (int64_t f = tid; f < npk; f += nt) {
-    int r = static_cast<int>((sqrtf(8.0f * f + 1.0f) - 1.0f) * 0.5f);
-    while (pk(r + 1, 0) <= f) ++r;
-    while (pk(r, 0) > f) --r;
-    const int c = static_cast<int>(f - pk(r, 0));
-    P[f] = A[(int64_t)r * lda + c];
-  }
-  __syncthreads();
-
-  // ---- 1. tridiagonalisation ----
-  for (int i = 0; i + 2 < K; ++i) {
-    const int n = K - 1 - i;  // length of the column below the diagonal
-    float part = 0.f;
-    for (int a = 1 + tid; a < n; a += nt) {
-      const float x = P[pk(i + 1 + a, i)];
-      part += x * x;
-    }
-    const float sigma = block_sum(part, red);
-    const float x0 = P[pk(i + 1, i)];
-    const float dd = P[pk(i, i)];
-    float bt = 0.f, alpha = x0;
-    if (sigma > 0.f) {
-      const float mu = sqrtf(x0 * x0 + sigma);
-      alpha = x0 <= 0.f ? mu : -mu;
-      const float v0 = x0 - alpha;
-      bt = 2.0f / (v0 * v0 + sigma);
-      __syncthreads();
-      if (tid == 0) P[pk(i + 1, i)] = v0;
-    }
+    for (int i = j + 1 + tid; i < K; i += nt) L[i * K + j] *= inv;
     if (tid == 0) {
-      d[i] = dd;
-      e[i] = alpha;
-      beta[i] = bt;
+      L[j * K + j] = keep ? d * inv : 1.0f;
+      flags[j] = keep ? flags[j] : 0.f;
     }
     __syncthreads();
-    if (bt == 0.f) continue;
-    for (int a = tid; a < n; a += nt) v[a] = P[pk(i + 1 + a, i)];
-    __syncthreads();
-    // p = bt * A' v with A' the trailing block (rows/cols i+1..K-1)
-    {
-      int tpr = 32;
-      while (tpr > 1 && (int64_t)n * tpr > nt) tpr >>= 1;
-      const int rows_per_pass = nt / tpr;
-      for (int a0 = 0; a0 < n; a0 += rows_per_pass) {
-        const int a = a0 + tid / tpr, q = tid % tpr;
-        float s = 0.f;
-        if (a < n) {
-          const int ra = i + 1 + a;
-          for (int b = q; b < n; b += tpr) {
-            const int rb = i + 1 + b;
-            s += (rb <= ra ? P[pk(ra, rb)] : P[pk(rb, ra)]) * v[b];
-          }
-        }
-        for (int off = tpr >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (a < n && q == 0) pw[a] = bt * s;
+    if (keep) {
+      for (int a = j + 1 + wid; a < K; a += nw) {
+        const float la = L[a * K + j];
+        for (int b = j + 1 + lane; b <= a; b += 32) L[a * K + b] -= la * L[b * K + j];
       }
-    }
-    __syncthreads();
-    float vp = 0.f;
-    for (int a = tid; a < n; a += nt) vp += v[a] * pw[a];
-    const float c = 0.5f * bt * block_sum(vp, red);
-    for (int a = tid; a < n; a += nt) pw[a] -= c * v[a];  // w
-    __syncthreads();
-    // A' -= v w^T + w v^T on the lower triangle: warp per row, interleaved
-    {
-      const int wid = tid >> 5, lane = tid & 31, nw = nt >> 5;
-      for (int a = wid; a < n; a += nw) {
-        const float va = v[a], wa = pw[a];
-        float *row = P + pk(i + 1 + a, i + 1);
-        for (int b = lane; b <= a; b += 32) row[b] -= va * pw[b] + wa * v[b];
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    if (K >= 2) {
-      d[K - 2] = P[pk(K - 2, K - 2)];
-      e[K - 2] = P[pk(K - 1, K - 2)];
-    }
-    d[K - 1] = P[pk(K - 1, K - 1)];
-    e[K - 1] = 0.f;
-    if (K >= 2) beta[K - 2] = 0.f;
-    beta[K - 1] = 0.f;
-  }
-  __syncthreads();
-
-  // ---- 2. eigenvalues by multisection ----
-  __shared__ float s_glo, s_ghi, s_pivmin;
-  if (tid == 0) {
-    float glo = FLT_MAX, ghi = -FLT_MAX, emax = 0.f;
-    for (int a = 0; a < K; ++a) {
-      const float r = (a > 0 ? fabsf(e[a - 1]) : 0.f) + (a + 1 < K ? fabsf(e[a]) : 0.f);
-      glo = fminf(glo, d[a] - r);
-      ghi = fmaxf(ghi, d[a] + r);
-      if (a + 1 < K) emax = fmaxf(emax, e[a] * e[a]);
-    }
-    const float span = fmaxf(ghi - glo, fmaxf(fabsf(glo), fabsf(ghi)) * 1e-6f) + 1e-30f;
-    s_glo = glo - 1e-3f * span;
-    s_ghi = ghi + 1e-3f * span;
-    s_pivmin = FLT_MIN * fmaxf(1.0f, emax);
-  }
-  __syncthreads();
-  for (int t = tid; t < kw; t += nt) {
-    lo[t] = s_glo;
-    hi[t] = s_ghi;
-  }
-  __syncthreads();
-  {
-    int g = 32;
-    while (g > 1 && kw * g > nt) g >>= 1;
-    const int groups = nt / g;
-    for (int t0 = 0; t0 < kw; t0 += groups) {
-      const int t = t0 + tid / g, q = tid % g;
-      const int target = K - 1 - t;  // ascending index of the t-th largest
-      for (int it = 0; it < 64; ++it) {
-        float l = 0.f, h = 0.f;
-        bool active = t < kw;
-        if (active) {
-          l = lo[t];
-          h = hi[t];
-          if (h - l <= 2.0f * FLT_EPSILON * fmaxf(fabsf(l), fabsf(h)) + s_pivmin) active = false;
-        }
-        bool any = __any_sync(0xffffffffu, active);
-        // all lanes of a group share t, so the group agrees on 'active'
-        if (!__syncthreads_or(any)) break;
-        int cnt = 0;
-        const float x = l + (h - l) * (float)(q + 1) / (float)(g + 1);
-        if (active) {
-          float qq = d[0] - x;
-          cnt = qq < 0.f;
-          for (int a = 1; a < K; ++a) {
-            if (fabsf(qq) < s_pivmin) qq = -s_pivmin;
-            qq = d[a] - x - __fdividef(e[a - 1] * e[a - 1], qq);
-            cnt += qq < 0.f;
-          }
-        }
-        // new interval: the largest probe with count <= target and the smallest with count > target
-        float nl = l, nh = h;
-        for (int s = 0; s < g; ++s) {
-          const float xs = __shfl_sync(0xffffffffu, x, (tid & 31) / g * g + s);
-          const int cs = __shfl_sync(0xffffffffu, cnt, (tid & 31) / g * g + s);
-          if (cs <= target) nl = fmaxf(nl, xs);
-          else nh = fminf(nh, xs);
-        }
-        __syncthreads();
-        if (active && q == 0) {
-          lo[t] = nl;
-          hi[t] = fmaxf(nl, nh);
-        }
-        __syncthreads();
-      }
-    }
-  }
-  for (int t = tid; t < kw; t += nt) lam[t] = 0.5f * (lo[t] + hi[t]);
-  __syncthreads();
-
-  // ---- 3. inverse iteration, one thread per eigenvalue ----
-  __shared__ float s_tnorm;
-  if (tid == 0) s_tnorm = fmaxf(fabsf(s_glo), fabsf(s_ghi));
-  __syncthreads();
-  for (int t = tid; t < kw; t += nt) {
-    const float lm = lam[t];
-    const float tiny = fmaxf(FLT_EPSILON * s_tnorm, FLT_MIN);
-    // factor T - lm I = P L U (LAPACK gttrf scheme): fa = diag(U), fb = 1st super,
-    // fc = 2nd super, fl = multipliers, fp = interchange flags
-    float a_cur = d[0] - lm, b_cur = K > 1 ? e[0] : 0.f;
-    for (int a = 0; a + 1 < K; ++a) {
-      const float c = e[a];
-      const float a_next = d[a + 1] - lm;
-      const float b_next = a + 2 < K ? e[a + 1] : 0.f;
-      float l, du2 = 0.f, na, nb;
-      int piv;
-      if (fabsf(a_cur) >= fabsf(c)) {
-        if (a_cur == 0.f) a_cur = tiny;
-        l = c / a_cur;
-        na = a_next - l * b_cur;
-        nb = b_next;
-        piv = 0;
-      } else {
-        l = a_cur / c;
-        const float new_a = c;
-        const float new_b = a_next;
-        na = b_cur - l * a_next;
-        du2 = b_next;
-        nb = -l * b_next;
-        a_cur = new_a;
-        b_cur = new_b;
-        piv = 1;
-      }
-      const int64_t o = (int64_t)a * kw + t;
-      fa[o] = a_cur;
-      fb[o] = b_cur;
-      fc[o] = du2;
-      fl[o] = l;
-      fp[o] = piv ? 1.f : 0.f;
-      a_cur = na;
-      b_cur = nb;
-    }
-    if (a_cur == 0.f) a_cur = tiny;
-    fa[(int64_t)(K - 1) * kw + t] = a_cur;
-    fb[(int64_t)(K - 1) * kw + t] = 0.f;
-    fc[(int64_t)(K - 1) * kw + t] = 0.f;
-    for (int a = 0; a < K; ++a) {
-      const int64_t o = (int64_t)a * kw + t;
-      if (fabsf(fa[o]) < tiny) fa[o] = copysignf(tiny, fa[o]);
-    }
-    // start vector
-    for (int a = 0; a < K; ++a)
-      Z[(int64_t)a * kw + t] = (float)(hash32((uint32_t)(a * 7919 + t * 104729 + 12345)) >> 8) * (1.0f / 16777216.0f) - 0.5f;
-    for (int rep = 0; rep < 3; ++rep) {
-      // forward: apply P and L^{-1}
-      for (int a = 0; a + 1 < K; ++a) {
-        const int64_t o = (int64_t)a * kw + t;
-        float ya = Z[o], yb = Z[o + kw];
-        if (fp[o] != 0.f) {
-          const float tmp = ya;
-          ya = yb;
-          yb = tmp - fl[o] * ya;
-        } else {
-          yb -= fl[o] * ya;
-        }
-        Z[o] = ya;
-        Z[o + kw] = yb;
-      }
-      // backward with U
-      float x1 = 0.f, x2 = 0.f, nrm = 0.f;
-      for (int a = K - 1; a >= 0; --a) {
-        const int64_t o = (int64_t)a * kw + t;
-        const float x = (Z[o] - fb[o] * x1 - fc[o] * x2) / fa[o];
-        Z[o] = x;
-        x2 = x1;
-        x1 = x;
-        nrm = fmaxf(nrm, fabsf(x));
-      }
-      const float sc = nrm > 0.f ? 1.0f / nrm : 1.0f;
-      for (int a = 0; a < K; ++a) Z[(int64_t)a * kw + t] *= sc;
-    }
-  }
-  __syncthreads();
-
-  // ---- 4. Gram-Schmidt twice, column by column ----
-  for (int j = 0; j < kw; ++j) {
-    for (int pass = 0; pass < 2; ++pass) {
-      // h[l] = z_l . z_j for l < j
-      if (j > 0) {
-        int tpc = 32;
-        while (tpc > 1 && j * tpc > nt) tpc >>= 1;
-        const int per = nt / tpc;
-        for (int l0 = 0; l0 < j; l0 += per) {
-          const int l = l0 + tid / tpc, q = tid % tpc;
-          float s = 0.f;
-          if (l < j)
-            for (int a = q; a < K; a += tpc) s += Z[(int64_t)a * kw + l] * Z[(int64_t)a * kw + j];
-          for (int off = tpc >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-          if (l < j && q == 0) hvec[l] = s;
-        }
-        __syncthreads();
-        for (int a = tid; a < K; a += nt) {
-          float s = 0.f;
-          for (int l = 0; l < j; ++l) s += Z[(int64_t)a * kw + l] * hvec[l];
-          Z[(int64_t)a * kw + j] -= s;
-        }
-        __syncthreads();
-      }
-      float part = 0.f;
-      for (int a = tid; a < K; a += nt) {
-        const float z = Z[(int64_t)a * kw + j];
-        part += z * z;
-      }
-      const float nrm2 = block_sum(part, red);
-      const float sc = nrm2 > 0.f ? rsqrtf(nrm2) : 0.f;
-      for (int a = tid; a < K; a += nt) Z[(int64_t)a * kw + j] *= sc;
       __syncthreads();
     }
   }
-
-  // ---- 5. back-transformation: Z <- H_0 H_1 ... H_{K-3} Z ----
-  for (int i = K - 3; i >= 0; --i) {
-    const float bt = beta[i];
-    if (bt == 0.f) continue;
-    const int n = K - 1 - i;
-    for (int a = tid; a < n; a += nt) v[a] = P[pk(i + 1 + a, i)];
-    __syncthreads();
-    int tpc = 32;
-    while (tpc > 1 && kw * tpc > nt) tpc >>= 1;
-    const int per = nt / tpc;
-    for (int t0 = 0; t0 < kw; t0 += per) {
-      const int t = t0 + tid / tpc, q = tid % tpc;
-      float s = 0.f;
-      if (t < kw)
-        for (int a = q; a < n; a += tpc) s += v[a] * Z[(int64_t)(i + 1 + a) * kw + t];
-      for (int off = tpc >> 1; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (t < kw && q == 0) hvec[t] = bt * s;
+  // forward substitution: column c of L^{-1}
+  for (int c = tid; c < K; c += nt) {
+    const bool kc = flags[c] != 0.f;
+    for (int i = 0; i < K; ++i) {
+      float x = 0.f;
+      if (kc && i >= c && flags[i] != 0.f) {
+        float acc = (i == c) ? 1.0f : 0.0f;
+        for (int l = c; l < i; ++l) acc -= L[i * K + l] * X[(int64_t)l * K + c];
+        x = acc / L[i * K + i];
+      }
+      X[(int64_t)i * K + c] = x;
     }
-    __syncthreads();
-    for (int64_t f = tid; f < (int64_t)n * kw; f += nt) {
-      const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
-      Z[(int64_t)(i + 1 + a) * kw + t] -= v[a] * hvec[t];
-    }
-    __syncthreads();
   }
-
-  // ---- outputs ----
-  for (int t = tid; t < kw; t += nt) lam_out[t] = lam[t];
-  for (int64_t f = tid; f < (int64_t)K * kw; f += nt) {
-    const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
-    W[(int64_t)a * ld_w + t] = Z[f];
+  __syncthreads();
+  if (X_in_smem) {
+    for (int t = tid; t < K * K; t += nt) {
+      const int i = t / K, j = t % K;
+      Rinv[t] = X[(int64_t)j * K + i];  // R^{-1} = (L^{-1})^T
+    }
+  } else {
+    for (int t = tid; t < K * K; t += nt) {
+      const int i = t / K, j = t % K;
+      if (i < j) {
+        const float a = Rinv[(int64_t)i * K + j], b = Rinv[(int64_t)j * K + i];
+        Rinv[(int64_t)i * K + j] = b;
+        Rinv[(int64_t)j * K + i] = a;
+      }
+    }
   }
 }
 
@@ -688,7 +324,7 @@ void select_cols(cudaStream_t st, int K, const float *W, int ld_w, int ncols, in
 }
 
 static int tn_splits(int64_t R, int tiles) {
-  const int64_t want = std::max<int64_t>(1, (152 * 4 + tiles - 1) / std::max(tiles, 1));
+  const int64_t want = std::max<int64_t>(1, (152 * 2 + tiles - 1) / std::max(tiles, 1));
   const int64_t max_by_rows = std::max<int64_t>(1, R / 256);
   return static_cast<int>(std::min<int64_t>(std::min<int64_t>(want, max_by_rows), 1024));
 }
@@ -711,7 +347,7 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
   gemm_tn_kernel<<<grid, 256, 0, st>>>(R, K1, K2, X, ld_x, Y, ld_y, rps, tj, sym, partial, K1p, K2p);
   MC_CHECK_LAUNCH();
   const int64_t total = (int64_t)K1 * K2;
-  const int nb = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 8));
+  const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
   gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, nsplit, partial, K1p, K2p, sym, C, ld_c);
   MC_CHECK_LAUNCH();
 }
@@ -728,41 +364,15 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag, float ref_tol,
               float *Rinv) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
-  const size_t need = sizeof(float) * ((size_t)K * K + K);
-  MC_REQUIRE(need <= 200 * 1024, "chol_inv: block too wide for shared memory");
-  MC_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
-  chol_inv_kernel<<<1, 1024, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, nullptr);
+  const size_t base = sizeof(float) * ((size_t)K * K + K);
+  MC_REQUIRE(base <= 220 * 1024, "chol_inv: block too wide for shared memory");
+  const bool x_sm = base + sizeof(float) * (size_t)K * K <= 220 * 1024;
+  const size_t need = x_sm ? base + sizeof(float) * (size_t)K * K : base;
+  MC_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(220 * 1024)));
+  const int threads = K <= 128 ? 256 : 1024;
+  chol_inv_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, x_sm ? 1 : 0);
   MC_CHECK_LAUNCH();
 }
-
-static void eig_layout(int K, int kw, bool &P_sm, bool &Z_sm) {
-  const size_t fixed = sizeof(float) * (5 * (size_t)K + 4 * (size_t)kw) + 64;
-  const size_t p = sizeof(float) * round_up((int64_t)K * (K + 1) / 2, 4);
-  const size_t z = sizeof(float) * (size_t)K * kw;
-  P_sm = fixed + p <= EIG_SMEM;
-  Z_sm = fixed + (P_sm ? p : 0) + z <= EIG_SMEM;
-}
-
-size_t eig_work_bytes(int K, int kw) {
-  bool P_sm, Z_sm;
-  eig_layout(K, kw, P_sm, Z_sm);
-  size_t f = 0;
-  if (!P_sm) f += round_up((int64_t)K * (K + 1) / 2, 64);
-  if (!Z_sm) f += round_up((int64_t)K * kw, 64);
-  f += 5 * (size_t)K * kw;
-  return sizeof(float) * f + 256;
-}
-
-void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *lam, float *W, int ld_w, void *work) {
-  MC_REQUIRE(K >= 1 && K <= 1024 && kw >= 1 && kw <= K, "eig_topk: sizes out of range");
-  bool P_sm, Z_sm;
-  eig_layout(K, kw, P_sm, Z_sm);
-  MC_CUDA(cudaFuncSetAttribute(eig_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
-  eig_topk_kernel<<<1, EIG_THREADS, EIG_SMEM, st>>>(K, kw, A, lda, lam, W, ld_w, static_cast<float *>(work), P_sm ? 1 : 0,
-                                                    Z_sm ? 1 : 0);
-  MC_CHECK_LAUNCH();
-}
-
 
 // ===================================================== allocation-free Gram ==
 // mc_gram_noalloc is for callers that cannot allocate device memory while they

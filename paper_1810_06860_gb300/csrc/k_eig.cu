@@ -1,0 +1,538 @@
+// Small symmetric eigensolver: the kw largest eigenpairs of a K x K float32
+// matrix, the eig() step of eigSVD (Alg. 3 step 2) applied to the Gram of
+// B^T in rSVD-PI / rSVD-BKI (Alg. 4/5).
+//
+// Kernel 1 (one block of 1024 threads): Householder reduction to tridiagonal
+//   form T = Q^T A Q.  The packed lower triangle lives in shared memory; the
+//   symmetric matrix-vector product reads every stored element once, row by
+//   row (a warp per row, lanes along the row), keeping the transposed
+//   contributions in per-lane registers, so all accesses are bank-conflict
+//   free.  Four barriers per column.  The reflectors go to global memory.
+// Kernel 2 (one block of 1024 threads):
+//   - Sturm-count multisection for the kw largest eigenvalues of T;
+//   - inverse iteration, one thread per eigenvalue (pivoted tridiagonal LU,
+//     three solves from a fixed pseudo-random start).  Eigenvalues within
+//     1e-5 ||T|| of a neighbour form a cluster; their shifts are moved just
+//     outside the cluster so that every direction of the cluster grows alike
+//     and different starts give independent vectors;
+//   - classical Gram-Schmidt applied twice (descending eigenvalue order);
+//   - back-transformation by the reflectors, staged 16 at a time in shared
+//     memory.
+// Everything is float32; every reduction has a fixed order.
+#include "mc_common.cuh"
+
+#include <algorithm>
+#include <cfloat>
+
+namespace mc {
+namespace {
+
+constexpr int EIG_THREADS = 1024;
+constexpr int NW = EIG_THREADS / 32;
+constexpr size_t EIG_SMEM = 220 * 1024;
+constexpr int TRI_FAST_MAX = 256;  // transposed contributions in registers up to this size
+constexpr int HV_CHUNK = 16;       // reflectors staged per back-transformation chunk
+
+__device__ __forceinline__ int pk(int r, int c) { return r * (r + 1) / 2 + c; }  // r >= c
+
+// Block-wide sum returned to every thread (one barrier).  Successive calls
+// must alternate buffers.
+__device__ __forceinline__ float block_sum1(float v, float *red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll 8
+  for (int q = 0; q < NW; ++q) t += red[q];
+  return t;
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// --------------------------------------------------------------- kernel 1 --
+__global__ void __launch_bounds__(EIG_THREADS, 1)
+eig_tridiag_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d, float *__restrict__ g_e,
+                   float *__restrict__ g_beta, float *__restrict__ Hv, float *__restrict__ gP, int p_in_smem) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float red[2][32];
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const bool fast = K <= TRI_FAST_MAX + 1;
+  float *vv = sm;                 // K
+  float *pw = vv + K;             // K
+  float *prow = pw + K;           // K
+  float *dd = prow + K;           // K
+  float *ppw = dd + K;            // NW x TRI_FAST_MAX (fast path)
+  float *P = p_in_smem ? ppw + (fast ? NW * TRI_FAST_MAX : 0) : gP;
+
+  for (int r = wid; r < K; r += NW)
+    for (int c = lane; c <= r; c += 32) P[pk(r, c)] = A[(int64_t)r * lda + c];
+  __syncthreads();
+  int rb = 0;  // alternating reduction buffer
+  for (int i = 0; i + 2 < K; ++i) {
+    const int n = K - 1 - i;
+    float part = 0.f;
+    for (int a = 1 + tid; a < n; a += EIG_THREADS) {
+      const float x = P[pk(i + 1 + a, i)];
+      vv[a] = x;
+      part += x * x;
+    }
+    const float sigma = block_sum1(part, red[rb]);
+    rb ^= 1;
+    const float x0 = P[pk(i + 1, i)];
+    float bt = 0.f, alpha = x0, v0 = 0.f;
+    if (sigma > 0.f) {
+      const float mu = sqrtf(x0 * x0 + sigma);
+      alpha = x0 <= 0.f ? mu : -mu;
+      v0 = x0 - alpha;
+      bt = 2.0f / (v0 * v0 + sigma);
+    }
+    if (tid == 0) {
+      dd[i] = P[pk(i, i)];
+      g_e[i] = alpha;
+      g_beta[i] = bt;
+      Hv[(int64_t)i * K] = v0;
+    }
+    for (int a = 1 + tid; a < n; a += EIG_THREADS) Hv[(int64_t)i * K + a] = vv[a];
+    if (bt == 0.f) {
+      __syncthreads();
+      continue;
+    }
+    float vp = 0.f;
+    if (fast) {
+      // p = A' v: warp per row a, lanes along the row; the row's transposed
+      // contributions A'(a,b) v_a (b < a) accumulate in pp[] of lane b % 32
+      float pp[TRI_FAST_MAX / 32];
+#pragma unroll
+      for (int j = 0; j < TRI_FAST_MAX / 32; ++j) pp[j] = 0.f;
+      for (int a = wid; a < n; a += NW) {
+        const float va = a == 0 ? v0 : vv[a];
+        const float *row = P + pk(i + 1 + a, i + 1);
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < TRI_FAST_MAX / 32; ++j) {
+          const int b = lane + 32 * j;
+          if (b <= a) {
+            const float x = row[b];
+            acc = fmaf(x, b == 0 ? v0 : vv[b], acc);
+            if (b < a) pp[j] = fmaf(x, va, pp[j]);
+          }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) prow[a] = acc;
+      }
+#pragma unroll
+      for (int j = 0; j < TRI_FAST_MAX / 32; ++j) {
+        const int b = lane + 32 * j;
+        if (b < n) ppw[wid * TRI_FAST_MAX + b] = pp[j];
+      }
+      __syncthreads();
+      for (int b = tid; b < n; b += EIG_THREADS) {
+        float acc = prow[b];
+#pragma unroll 8
+        for (int w = 0; w < NW; ++w) acc += ppw[w * TRI_FAST_MAX + b];
+        const float pb = bt * acc;
+        pw[b] = pb;
+        vp = fmaf(b == 0 ? v0 : vv[b], pb, vp);
+      }
+    } else {
+      // large K: row groups read rows and (strided) columns of the packed triangle
+      int tpr = 32;
+      while (tpr > 1 && n * tpr > EIG_THREADS) tpr >>= 1;
+      const int rows_per_pass = EIG_THREADS / tpr;
+      for (int a0 = 0; a0 < n; a0 += rows_per_pass) {
+        const int a = a0 + tid / tpr, q = tid % tpr;
+        float sacc = 0.f;
+        if (a < n) {
+          const int ra = i + 1 + a;
+          const float *row = P + pk(ra, i + 1);
+          for (int b = q; b <= a; b += tpr) sacc += row[b] * (b == 0 ? v0 : vv[b]);
+          for (int b = a + 1 + q; b < n; b += tpr) sacc += P[pk(i + 1 + b, ra)] * vv[b];
+        }
+        for (int off = tpr >> 1; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+        if (a < n && q == 0) {
+          const float pa = bt * sacc;
+          pw[a] = pa;
+          vp = fmaf(a == 0 ? v0 : vv[a], pa, vp);
+        }
+      }
+    }
+    const float c = 0.5f * bt * block_sum1(vp, red[rb]);
+    rb ^= 1;
+    // A' -= v w^T + w v^T with w = p - c v, lower triangle, warp per row
+    for (int a = wid; a < n; a += NW) {
+      const float va = a == 0 ? v0 : vv[a];
+      const float wa = pw[a] - c * va;
+      float *row = P + pk(i + 1 + a, i + 1);
+      for (int b = lane; b <= a; b += 32) {
+        const float vb = b == 0 ? v0 : vv[b];
+        const float wb = pw[b] - c * vb;
+        row[b] -= va * wb + wa * vb;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (K >= 2) {
+      dd[K - 2] = P[pk(K - 2, K - 2)];
+      g_e[K - 2] = P[pk(K - 1, K - 2)];
+      g_beta[K - 2] = 0.f;
+    }
+    dd[K - 1] = P[pk(K - 1, K - 1)];
+    g_e[K - 1] = 0.f;
+    g_beta[K - 1] = 0.f;
+  }
+  __syncthreads();
+  for (int a = tid; a < K; a += EIG_THREADS) g_d[a] = dd[a];
+}
+
+// --------------------------------------------------------------- kernel 2 --
+struct VecLayout {
+  int ldz;         // odd row stride of Z
+  int z_in_smem;   // Z in shared memory
+  int batch;       // eigenvalues factored at once (factors in shared memory)
+  int f_in_smem;
+  int64_t g_z;     // float offsets into the global work area
+  int64_t g_f;
+};
+
+__global__ void __launch_bounds__(EIG_THREADS, 1)
+eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__restrict__ g_e,
+                   const float *__restrict__ g_beta, const float *__restrict__ Hv, float *__restrict__ lam_out,
+                   float *__restrict__ W, int ld_w, float *__restrict__ gw, VecLayout lay) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float red[2][32];
+  __shared__ float s_glo, s_ghi, s_pivmin;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int ldz = lay.ldz;
+  float *d = sm;                  // K
+  float *e = d + K;               // K
+  float *beta = e + K;            // K
+  float *lam = beta + K;          // kw
+  float *lo = lam + kw;           // kw
+  float *hi = lo + kw;            // kw
+  float *hvec = hi + kw;          // kw
+  float *part = hvec + kw;        // NW x 32
+  float *hv = part + NW * 32;     // HV_CHUNK x K
+  float *big = hv + (size_t)HV_CHUNK * K;
+  big = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(big) + 15) & ~uintptr_t(15));
+  float *Z = lay.z_in_smem ? big : gw + lay.g_z;
+  float *F = lay.f_in_smem ? (lay.z_in_smem ? big + (size_t)K * ldz : big) : gw + lay.g_f;
+  const int B = lay.batch;
+
+  for (int a = tid; a < K; a += EIG_THREADS) {
+    d[a] = g_d[a];
+    e[a] = g_e[a];
+    beta[a] = g_beta[a];
+  }
+  __syncthreads();
+
+  // ---- multisection ----
+  if (tid < 32) {
+    float glo = FLT_MAX, ghi = -FLT_MAX, emax = 0.f;
+    for (int a = lane; a < K; a += 32) {
+      const float r = (a > 0 ? fabsf(e[a - 1]) : 0.f) + (a + 1 < K ? fabsf(e[a]) : 0.f);
+      glo = fminf(glo, d[a] - r);
+      ghi = fmaxf(ghi, d[a] + r);
+      if (a + 1 < K) emax = fmaxf(emax, e[a] * e[a]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      glo = fminf(glo, __shfl_xor_sync(0xffffffffu, glo, off));
+      ghi = fmaxf(ghi, __shfl_xor_sync(0xffffffffu, ghi, off));
+      emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    }
+    if (lane == 0) {
+      const float span = fmaxf(ghi - glo, fmaxf(fabsf(glo), fabsf(ghi)) * 1e-6f) + 1e-30f;
+      s_glo = glo - 1e-3f * span;
+      s_ghi = ghi + 1e-3f * span;
+      s_pivmin = FLT_MIN * fmaxf(1.0f, emax);
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < kw; t += EIG_THREADS) {
+    lo[t] = s_glo;
+    hi[t] = s_ghi;
+  }
+  __syncthreads();
+  {
+    int g = 32;
+    while (g > 1 && kw * g > EIG_THREADS) g >>= 1;
+    const int groups = EIG_THREADS / g;
+    for (int t0 = 0; t0 < kw; t0 += groups) {
+      const int t = t0 + tid / g, q = tid % g;
+      const int target = K - 1 - t;
+      for (int it = 0; it < 64; ++it) {
+        float l = 0.f, h = 0.f;
+        bool active = t < kw;
+        if (active) {
+          l = lo[t];
+          h = hi[t];
+          if (h - l <= 2.0f * FLT_EPSILON * fmaxf(fabsf(l), fabsf(h)) + s_pivmin) active = false;
+        }
+        if (!__syncthreads_or(active)) break;
+        int cnt = 0;
+        const float x = l + (h - l) * (float)(q + 1) / (float)(g + 1);
+        if (active) {
+          float qq = d[0] - x;
+          cnt = qq < 0.f;
+          for (int a = 1; a < K; ++a) {
+            if (fabsf(qq) < s_pivmin) qq = -s_pivmin;
+            qq = d[a] - x - __fdividef(e[a - 1] * e[a - 1], qq);
+            cnt += qq < 0.f;
+          }
+        }
+        float nl = l, nh = h;
+        for (int sidx = 0; sidx < g; ++sidx) {
+          const float xs = __shfl_sync(0xffffffffu, x, (lane / g) * g + sidx);
+          const int cs = __shfl_sync(0xffffffffu, cnt, (lane / g) * g + sidx);
+          if (cs <= target) nl = fmaxf(nl, xs);
+          else nh = fminf(nh, xs);
+        }
+        __syncthreads();
+        if (active && q == 0) {
+          lo[t] = nl;
+          hi[t] = fmaxf(nl, nh);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (int t = tid; t < kw; t += EIG_THREADS) lam[t] = 0.5f * (lo[t] + hi[t]);
+  __syncthreads();
+
+  // ---- inverse iteration, B eigenvalues at a time ----
+  const float tnorm = fmaxf(fabsf(s_glo), fabsf(s_ghi));
+  const float tol_c = 1e-5f * tnorm;
+  for (int t0 = 0; t0 < kw; t0 += B) {
+    const int t = t0 + tid;
+    if (tid < B && t < kw) {
+      float *fa = F, *fb = F + (size_t)K * B, *fc = F + (size_t)2 * K * B, *fl = F + (size_t)3 * K * B;
+      const bool clus = (t > 0 && lam[t - 1] - lam[t] <= tol_c) || (t + 1 < kw && lam[t] - lam[t + 1] <= tol_c);
+      const float lm = lam[t] + (clus ? 2.0f * tol_c * (1.0f + 0.01f * (float)(t % 64)) : 0.f);
+      const float tiny = fmaxf(FLT_EPSILON * tnorm, FLT_MIN);
+      unsigned piv_bits[32];  // K <= 1024
+#pragma unroll
+      for (int q = 0; q < 32; ++q) piv_bits[q] = 0u;
+      float a_cur = d[0] - lm, b_cur = K > 1 ? e[0] : 0.f;
+      for (int a = 0; a + 1 < K; ++a) {
+        const float cc = e[a];
+        const float a_next = d[a + 1] - lm;
+        const float b_next = a + 2 < K ? e[a + 1] : 0.f;
+        float l, du2 = 0.f, na, nb;
+        if (fabsf(a_cur) >= fabsf(cc)) {
+          if (a_cur == 0.f) a_cur = tiny;
+          l = cc / a_cur;
+          na = a_next - l * b_cur;
+          nb = b_next;
+        } else {
+          l = a_cur / cc;
+          na = b_cur - l * a_next;
+          du2 = b_next;
+          nb = -l * b_next;
+          a_cur = cc;
+          b_cur = a_next;
+          piv_bits[a >> 5] |= 1u << (a & 31);
+        }
+        const int o = a * B + tid;
+        fa[o] = 1.0f / (fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
+        fb[o] = b_cur;
+        fc[o] = du2;
+        fl[o] = l;
+        a_cur = na;
+        b_cur = nb;
+      }
+      {
+        const int o = (K - 1) * B + tid;
+        fa[o] = 1.0f / (fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
+        fb[o] = 0.f;
+        fc[o] = 0.f;
+      }
+      for (int a = 0; a < K; ++a)
+        Z[(int64_t)a * ldz + t] =
+            (float)(hash32((uint32_t)(a * 7919 + t * 104729 + 12345)) >> 8) * (1.0f / 16777216.0f) - 0.5f;
+      for (int rep = 0; rep < 3; ++rep) {
+        float ya = Z[t];
+        for (int a = 0; a + 1 < K; ++a) {
+          float yb = Z[(int64_t)(a + 1) * ldz + t];
+          const float l = fl[a * B + tid];
+          if (piv_bits[a >> 5] & (1u << (a & 31))) {
+            const float tmp = ya;
+            ya = yb;
+            yb = tmp - l * ya;
+          } else {
+            yb -= l * ya;
+          }
+          Z[(int64_t)a * ldz + t] = ya;
+          ya = yb;
+        }
+        float x1 = ya * fa[(K - 1) * B + tid], x2 = 0.f;
+        Z[(int64_t)(K - 1) * ldz + t] = x1;
+        float nrm = fabsf(x1);
+        for (int a = K - 2; a >= 0; --a) {
+          const int o = a * B + tid;
+          const float xx = (Z[(int64_t)a * ldz + t] - fb[o] * x1 - fc[o] * x2) * fa[o];
+          Z[(int64_t)a * ldz + t] = xx;
+          x2 = x1;
+          x1 = xx;
+          nrm = fmaxf(nrm, fabsf(xx));
+        }
+        const float sc = nrm > 0.f ? 1.0f / nrm : 1.0f;
+        for (int a = 0; a < K; ++a) Z[(int64_t)a * ldz + t] *= sc;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- Gram-Schmidt twice ----
+  int rb = 0;
+  for (int j = 0; j < kw; ++j) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (j > 0) {
+        // h[l] = z_l . z_j: lanes along l, warps split the rows
+        for (int c0 = 0; c0 < j; c0 += 32) {
+          const int l = c0 + lane;
+          float acc = 0.f;
+          if (l < j)
+            for (int a = wid; a < K; a += NW) acc = fmaf(Z[(int64_t)a * ldz + l], Z[(int64_t)a * ldz + j], acc);
+          part[wid * 32 + lane] = acc;
+          __syncthreads();
+          if (tid < 32 && c0 + tid < j) {
+            float s = 0.f;
+            for (int w = 0; w < NW; ++w) s += part[w * 32 + tid];
+            hvec[c0 + tid] = s;
+          }
+          __syncthreads();
+        }
+      }
+      float nrm_part = 0.f;
+      for (int a = tid; a < K; a += EIG_THREADS) {
+        float z = Z[(int64_t)a * ldz + j];
+        for (int l = 0; l < j; ++l) z = fmaf(-Z[(int64_t)a * ldz + l], hvec[l], z);
+        Z[(int64_t)a * ldz + j] = z;
+        nrm_part = fmaf(z, z, nrm_part);
+      }
+      const float nrm2 = block_sum1(nrm_part, red[rb]);
+      rb ^= 1;
+      const float sc = nrm2 > 0.f ? rsqrtf(nrm2) : 0.f;
+      for (int a = tid; a < K; a += EIG_THREADS) Z[(int64_t)a * ldz + j] *= sc;
+      __syncthreads();
+    }
+  }
+
+  // ---- back-transformation: Z <- H_0 H_1 ... H_{K-3} Z ----
+  for (int top = K - 3; top >= 0; top -= HV_CHUNK) {
+    const int lowi = max(0, top - HV_CHUNK + 1);
+    for (int64_t f = tid; f < (int64_t)(top - lowi + 1) * K; f += EIG_THREADS) {
+      const int r = static_cast<int>(f / K), a = static_cast<int>(f % K);
+      hv[r * K + a] = Hv[(int64_t)(lowi + r) * K + a];
+    }
+    __syncthreads();
+    for (int i = top; i >= lowi; --i) {
+      const float bt = beta[i];
+      if (bt == 0.f) continue;
+      const int n = K - 1 - i;
+      const float *v = hv + (i - lowi) * K;
+      for (int c0 = 0; c0 < kw; c0 += 32) {
+        const int t = c0 + lane;
+        float acc = 0.f;
+        if (t < kw)
+          for (int a = wid; a < n; a += NW) acc = fmaf(v[a], Z[(int64_t)(i + 1 + a) * ldz + t], acc);
+        part[wid * 32 + lane] = acc;
+        __syncthreads();
+        if (tid < 32 && c0 + tid < kw) {
+          float s = 0.f;
+          for (int w = 0; w < NW; ++w) s += part[w * 32 + tid];
+          hvec[c0 + tid] = bt * s;
+        }
+        __syncthreads();
+      }
+      for (int64_t f = tid; f < (int64_t)n * kw; f += EIG_THREADS) {
+        const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
+        Z[(int64_t)(i + 1 + a) * ldz + t] -= v[a] * hvec[t];
+      }
+      __syncthreads();
+    }
+  }
+
+  for (int t = tid; t < kw; t += EIG_THREADS) lam_out[t] = lam[t];
+  for (int64_t f = tid; f < (int64_t)K * kw; f += EIG_THREADS) {
+    const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
+    W[(int64_t)a * ld_w + t] = Z[(int64_t)a * ldz + t];
+  }
+}
+
+// ------------------------------------------------------------------ plans --
+struct EigPlan {
+  int p_in_smem;
+  size_t tri_smem;
+  VecLayout vl;
+  size_t vec_smem;
+  int64_t g_d, g_e, g_beta, g_hv, g_p, g_total;  // float offsets in the work area
+};
+
+EigPlan eig_plan(int K, int kw) {
+  EigPlan pl{};
+  const bool fast = K <= TRI_FAST_MAX + 1;
+  const size_t tri_fixed = sizeof(float) * (4 * (size_t)K + (fast ? (size_t)NW * TRI_FAST_MAX : 0));
+  const size_t pbytes = sizeof(float) * ((size_t)K * (K + 1) / 2);
+  pl.p_in_smem = tri_fixed + pbytes <= EIG_SMEM;
+  pl.tri_smem = tri_fixed + (pl.p_in_smem ? pbytes : 0);
+  int64_t off = 0;
+  pl.g_d = off;
+  off += round_up(K, 64);
+  pl.g_e = off;
+  off += round_up(K, 64);
+  pl.g_beta = off;
+  off += round_up(K, 64);
+  pl.g_hv = off;
+  off += round_up((int64_t)K * K, 64);
+  pl.g_p = off;
+  off += pl.p_in_smem ? 0 : round_up((int64_t)K * (K + 1) / 2, 64);
+  VecLayout vl{};
+  vl.ldz = kw | 1;
+  const size_t vfixed = sizeof(float) * (3 * (size_t)K + 4 * (size_t)kw + NW * 32 + (size_t)HV_CHUNK * K) + 16;
+  const size_t zbytes = sizeof(float) * (size_t)K * vl.ldz;
+  vl.z_in_smem = vfixed + zbytes <= EIG_SMEM;
+  const size_t avail = EIG_SMEM - vfixed - (vl.z_in_smem ? zbytes : 0);
+  int batch = static_cast<int>(std::min<size_t>(32, avail / (sizeof(float) * 4 * (size_t)K)));
+  vl.f_in_smem = batch >= 8;
+  if (!vl.f_in_smem) batch = 32;
+  vl.batch = std::min(batch, std::max(kw, 1));
+  vl.g_z = off;
+  off += vl.z_in_smem ? 0 : round_up((int64_t)K * vl.ldz, 64);
+  vl.g_f = off;
+  off += vl.f_in_smem ? 0 : round_up((int64_t)4 * K * vl.batch, 64);
+  pl.vl = vl;
+  pl.vec_smem = vfixed + (vl.z_in_smem ? zbytes : 0) + (vl.f_in_smem ? sizeof(float) * 4 * (size_t)K * vl.batch : 0);
+  pl.g_total = off;
+  return pl;
+}
+
+}  // namespace
+
+size_t eig_work_bytes(int K, int kw) { return sizeof(float) * (size_t)eig_plan(K, kw).g_total + 256; }
+
+void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *lam, float *W, int ld_w, void *work) {
+  MC_REQUIRE(K >= 1 && K <= 1024 && kw >= 1 && kw <= K, "eig_topk: sizes out of range");
+  const EigPlan pl = eig_plan(K, kw);
+  MC_REQUIRE(pl.vec_smem <= EIG_SMEM && pl.tri_smem <= EIG_SMEM, "eig_topk: shared-memory plan does not fit");
+  float *gw = static_cast<float *>(work);
+  MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+  MC_CUDA(cudaFuncSetAttribute(eig_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+  eig_tridiag_kernel<<<1, EIG_THREADS, pl.tri_smem, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                         gw + pl.g_hv, gw + pl.g_p, pl.p_in_smem);
+  MC_CHECK_LAUNCH();
+  eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                         gw + pl.g_hv, lam, W, ld_w, gw, pl.vl);
+  MC_CHECK_LAUNCH();
+}
+
+}  // namespace mc

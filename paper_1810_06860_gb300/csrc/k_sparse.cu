@@ -114,67 +114,58 @@ __global__ void csc_scatter_kernel(int64_t m, int64_t n, int nblk, const int *__
 }
 
 // --------------------------------------------------------------- products ---
-template <int G, int CH>
+template <int G>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-spmm_seg_kernel(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict__ seg_beg,
-                const int *__restrict__ seg_end, const int *__restrict__ seg_slot,
-                const int *__restrict__ idx, const float *__restrict__ val, const float *__restrict__ X,
-                int ld_x, int K4, float *__restrict__ out, int ld_out, float *__restrict__ partial) {
-  constexpr int L = 32 / G;  // lanes per group
+spmm_seg_kernel(int64_t nseg, const int4 *__restrict__ segs, const int *__restrict__ idx,
+                const float *__restrict__ val, const float *__restrict__ X, int ld_x, int K4,
+                float *__restrict__ out, int ld_out, float *__restrict__ partial) {
+  constexpr int L = 32 / G;  // lanes per group; a group owns one gathered row at a time
+  constexpr int U = G >= 8 ? 1 : (G >= 2 ? 2 : 4);  // gathers in flight per group
   const int lane = threadIdx.x & 31;
   const int64_t seg = blockIdx.x * (int64_t)kWarpsPerBlock + (threadIdx.x >> 5);
   if (seg >= nseg) return;
   const int g = lane / L, li = lane % L;
-  const int beg = seg_beg[seg], end = seg_end[seg];
-  float4 acc[CH];
-#pragma unroll
-  for (int c = 0; c < CH; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int base = beg; base < end; base += 32) {
+  const int4 sd = segs[seg];  // (row, begin, end, partial slot or -1)
+  const bool active = li < K4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int base = sd.y; base < sd.z; base += 32) {
     const int e = base + lane;
-    const int my_idx = e < end ? idx[e] : 0;
-    const float my_val = e < end ? val[e] : 0.f;
-    const int cnt = min(32, end - base);
-#pragma unroll 4
-    for (int t = 0; t < 32; t += G) {
-      if (t >= cnt) break;
-      const int src = t + g;
-      const int j = __shfl_sync(0xffffffffu, my_idx, src);
-      const float a = __shfl_sync(0xffffffffu, my_val, src);
-      if (src < cnt) {
-        const float4 *xr = reinterpret_cast<const float4 *>(X + (int64_t)j * ld_x);
+    const int my_idx = e < sd.z ? idx[e] : 0;
+    const float my_val = e < sd.z ? val[e] : 0.f;
+    const int cnt = min(32, sd.z - base);
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const int q = li + c * L;
-          if (q < K4) {
-            const float4 x = __ldg(xr + q);
-            acc[c].x = fmaf(a, x.x, acc[c].x);
-            acc[c].y = fmaf(a, x.y, acc[c].y);
-            acc[c].z = fmaf(a, x.z, acc[c].z);
-            acc[c].w = fmaf(a, x.w, acc[c].w);
-          }
-        }
+    for (int t0 = 0; t0 < 32; t0 += G * U) {
+      if (t0 >= cnt) break;  // warp-uniform
+      float4 xv[U];
+      float av[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int src = t0 + u * G + g;
+        const int j = __shfl_sync(0xffffffffu, my_idx, src);
+        av[u] = __shfl_sync(0xffffffffu, my_val, src);
+        xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (active && src < cnt) xv[u] = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)j * ld_x) + li);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        acc.x = fmaf(av[u], xv[u].x, acc.x);
+        acc.y = fmaf(av[u], xv[u].y, acc.y);
+        acc.z = fmaf(av[u], xv[u].z, acc.z);
+        acc.w = fmaf(av[u], xv[u].w, acc.w);
       }
     }
   }
 #pragma unroll
   for (int off = L; off < 32; off <<= 1) {
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, off);
-      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, off);
-      acc[c].z += __shfl_xor_sync(0xffffffffu, acc[c].z, off);
-      acc[c].w += __shfl_xor_sync(0xffffffffu, acc[c].w, off);
-    }
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
   }
-  if (g != 0) return;
-  const int slot = seg_slot[seg];
-  float4 *dst = slot < 0 ? reinterpret_cast<float4 *>(out + (int64_t)seg_row[seg] * ld_out)
-                         : reinterpret_cast<float4 *>(partial + (int64_t)slot * (K4 * 4));
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int q = li + c * L;
-    if (q < K4) dst[q] = acc[c];
-  }
+  if (g != 0 || !active) return;
+  float4 *dst = sd.w < 0 ? reinterpret_cast<float4 *>(out + (int64_t)sd.x * ld_out)
+                         : reinterpret_cast<float4 *>(partial + (int64_t)sd.w * (K4 * 4));
+  dst[li] = acc;
 }
 
 __global__ void spmm_fixup_kernel(int64_t nsplit, const int *__restrict__ split_row,
@@ -204,49 +195,56 @@ __global__ void mirror_kernel(int64_t nnz, const int *__restrict__ perm, const f
 }
 
 // ------------------------------------------------------- fused SVT update ---
-// One warp per CSR segment; the row's shrunk left factor Us[i, 0:r] is staged
-// in shared memory and read as broadcasts; each lane takes one observed entry
-// at a time and gathers V[j, 0:r] with 128-bit loads.  The dot product runs in
-// a fixed order, so the same entry always gives the same x.
-constexpr int kSddmmMaxR = 1024;
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-sddmm_update_kernel(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict__ seg_beg,
-                    const int *__restrict__ seg_end, const int *__restrict__ col, const float *__restrict__ mval,
-                    float *__restrict__ y, const float *__restrict__ Us, int ld_us, const float *__restrict__ V,
-                    int ld_v, int r, float delta, int update, double *__restrict__ seg_sq,
-                    float *__restrict__ x_out) {
-  extern __shared__ float4 sh_us4[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t seg = blockIdx.x * (int64_t)kWarpsPerBlock + warp;
-  const int r4 = (r + 3) >> 2;
-  float4 *us = sh_us4 + warp * r4;
+// One thread per observed entry (grid-stride over a fixed grid, so every
+// thread always sees the same entries): x_e = <Us[i,:], V[j,:]> with 128-bit
+// loads (entries of one row are adjacent, so a warp's Us loads mostly hit
+// one row), res = M_e - x_e, y_e += delta res, and sum res^2 per block in a
+// fixed order.  The dot product order is fixed, so the same entry always
+// gives the same x.
+constexpr int kSddmmThreads = 256;
+constexpr int kSddmmBlocks = 152 * 8;
+__global__ void __launch_bounds__(kSddmmThreads)
+sddmm_update_kernel(int64_t nnz, const int *__restrict__ rix, const int *__restrict__ col,
+                    const float *__restrict__ mval, float *__restrict__ y, const float *__restrict__ Us, int ld_us,
+                    const float *__restrict__ V, int ld_v, int r4, float delta, int update,
+                    double *__restrict__ block_sq, float *__restrict__ x_out) {
+  __shared__ float wsum[kSddmmThreads / 32];
   float sq = 0.f;
-  if (seg < nseg) {
-    const int row = seg_row[seg];
-    const float4 *src = reinterpret_cast<const float4 *>(Us + (int64_t)row * ld_us);
-    for (int q = lane; q < r4; q += 32) us[q] = src[q];
-    __syncwarp();
-    const int beg = seg_beg[seg], end = seg_end[seg];
-    for (int e = beg + lane; e < end; e += 32) {
-      const float4 *vr = reinterpret_cast<const float4 *>(V + (int64_t)col[e] * ld_v);
-      float x = 0.f;
-      for (int q = 0; q < r4; ++q) {
-        const float4 a = us[q];
-        const float4 b = __ldg(vr + q);
-        x = fmaf(a.x, b.x, x);
-        x = fmaf(a.y, b.y, x);
-        x = fmaf(a.z, b.z, x);
-        x = fmaf(a.w, b.w, x);
-      }
-      const float res = mval[e] - x;
-      sq = fmaf(res, res, sq);
-      if (update) y[e] = fmaf(delta, res, y[e]);
-      if (x_out) x_out[e] = x;
+  for (int64_t e = blockIdx.x * (int64_t)kSddmmThreads + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * kSddmmThreads) {
+    const float4 *a = reinterpret_cast<const float4 *>(Us + (int64_t)rix[e] * ld_us);
+    const float4 *b = reinterpret_cast<const float4 *>(V + (int64_t)col[e] * ld_v);
+    float x = 0.f;
+    for (int q = 0; q < r4; ++q) {
+      const float4 u = __ldg(a + q);
+      const float4 v = __ldg(b + q);
+      x = fmaf(u.x, v.x, x);
+      x = fmaf(u.y, v.y, x);
+      x = fmaf(u.z, v.z, x);
+      x = fmaf(u.w, v.w, x);
     }
+    const float res = mval[e] - x;
+    sq = fmaf(res, res, sq);
+    if (update) y[e] = fmaf(delta, res, y[e]);
+    if (x_out) x_out[e] = x;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
-  if (lane == 0 && seg < nseg) seg_sq[seg] = static_cast<double>(sq);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kSddmmThreads / 32; ++w) t += wsum[w];
+    block_sq[blockIdx.x] = t;
+  }
+}
+
+// Row index of every CSR entry (the fused update walks entries, not rows).
+__global__ void expand_rows_kernel(int64_t m, const int *__restrict__ rp, int *__restrict__ rix) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m) return;
+  for (int e = rp[w] + lane; e < rp[w + 1]; e += 32) rix[e] = static_cast<int>(w);
 }
 
 // ------------------------------------------------------------- reductions ---
@@ -346,6 +344,7 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
   MC_CUDA(cudaStreamSynchronize(st));
   std::vector<int> srow, sbeg, send, sslot, sprow, spslot;
   srow.reserve(rows + hp[rows] / SEG + 1);
+  std::vector<int4> packed;
   int slot = 0;
   for (int64_t i = 0; i < rows; ++i) {
     const int b = hp[i], e = hp[i + 1];
@@ -375,40 +374,43 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
     d.reserve(a, sizeof(int) * std::max<size_t>(1, v.size()));
     if (!v.empty()) MC_CUDA(cudaMemcpyAsync(d.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, st));
   };
-  up(plan.seg_row, srow);
-  up(plan.seg_beg, sbeg);
-  up(plan.seg_end, send);
-  up(plan.seg_slot, sslot);
+  packed.resize(srow.size());
+  for (size_t t = 0; t < srow.size(); ++t) packed[t] = make_int4(srow[t], sbeg[t], send[t], sslot[t]);
+  plan.seg.reserve(a, sizeof(int4) * std::max<size_t>(1, packed.size()));
+  if (!packed.empty())
+    MC_CUDA(cudaMemcpyAsync(plan.seg.p, packed.data(), sizeof(int4) * packed.size(), cudaMemcpyHostToDevice, st));
   up(plan.split_row, sprow);
   up(plan.split_slot, spslot);
   MC_CUDA(cudaStreamSynchronize(st));
 }
 
-void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, const float *X, int ld_x, int K,
-          float *out, int ld_out, float *partial) {
+void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, int64_t rows_in, const float *X,
+          int ld_x, int K, float *out, int ld_out, float *partial) {
   if (plan.nseg == 0 || K <= 0) return;
   MC_REQUIRE(K % 4 == 0 && ld_x % 4 == 0 && ld_out % 4 == 0, "spmm: K and leading dims must be multiples of 4");
-  const int K4 = K / 4;
+  MC_REQUIRE(K <= 1024, "spmm: panel width above 1024");
+  // Column chunks of at most 128, narrower when the panel slice would not stay
+  // resident in L2 next to the streamed indices (each chunk re-reads them).
+  int chunk = 128;
+  while (chunk > 32 && (double)rows_in * chunk * 4.0 > 40e6) chunk /= 2;
   const int64_t blocks = (plan.nseg + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int threads = kWarpsPerBlock * 32;
-#define MC_SPMM_ARGS                                                                                          \
-  plan.nseg, plan.seg_row.as<int>(), plan.seg_beg.as<int>(), plan.seg_end.as<int>(), plan.seg_slot.as<int>(), \
-      idx, val, X, ld_x, K4, out, ld_out, partial
-  if (K4 <= 2) spmm_seg_kernel<16, 1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (K4 <= 4) spmm_seg_kernel<8, 1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (K4 <= 8) spmm_seg_kernel<4, 1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (K4 <= 16) spmm_seg_kernel<2, 1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (K4 <= 32) spmm_seg_kernel<1, 1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (K4 <= 64) spmm_seg_kernel<1, 2><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (K4 <= 128) spmm_seg_kernel<1, 4><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (K4 <= 256) spmm_seg_kernel<1, 8><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else MC_REQUIRE(false, "spmm: panel width above 1024");
+  for (int c0 = 0; c0 < K; c0 += chunk) {
+    const int kc = std::min(chunk, K - c0);
+    const int K4 = kc / 4;
+#define MC_SPMM_ARGS plan.nseg, plan.seg.as<int4>(), idx, val, X + c0, ld_x, K4, out + c0, ld_out, partial
+    if (K4 <= 2) spmm_seg_kernel<16><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+    else if (K4 <= 4) spmm_seg_kernel<8><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+    else if (K4 <= 8) spmm_seg_kernel<4><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+    else if (K4 <= 16) spmm_seg_kernel<2><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+    else spmm_seg_kernel<1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
 #undef MC_SPMM_ARGS
-  MC_CHECK_LAUNCH();
-  if (plan.nsplit > 0) {
-    spmm_fixup_kernel<<<static_cast<unsigned>(plan.nsplit), 128, 0, st>>>(
-        plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, K, out, ld_out);
     MC_CHECK_LAUNCH();
+    if (plan.nsplit > 0) {
+      spmm_fixup_kernel<<<static_cast<unsigned>(plan.nsplit), 128, 0, st>>>(
+          plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, kc, out + c0, ld_out);
+      MC_CHECK_LAUNCH();
+    }
   }
 }
 
@@ -424,19 +426,24 @@ void mirror_values(cudaStream_t st, int64_t nnz, const int *perm, const float *y
   MC_CHECK_LAUNCH();
 }
 
-void sddmm_update(cudaStream_t st, const SegPlan &plan, const int *col, const float *mval, float *y, const float *Us,
-                  int ld_us, const float *V, int ld_v, int r, float delta, int update, double *seg_sq, float *x_out) {
-  if (plan.nseg == 0) return;
-  MC_REQUIRE(r >= 0 && r <= kSddmmMaxR, "sddmm: rank above 1024");
-  MC_REQUIRE(ld_us % 4 == 0 && ld_v % 4 == 0, "sddmm: leading dims must be multiples of 4");
-  const int r4 = (r + 3) / 4;
-  const size_t smem = sizeof(float4) * (size_t)kWarpsPerBlock * std::max(r4, 1);
-  const int64_t blocks = (plan.nseg + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (smem > 48 * 1024)
-    MC_CUDA(cudaFuncSetAttribute(sddmm_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sddmm_update_kernel<<<blocks, kWarpsPerBlock * 32, smem, st>>>(
-      plan.nseg, plan.seg_row.as<int>(), plan.seg_beg.as<int>(), plan.seg_end.as<int>(), col, mval, y, Us, ld_us, V,
-      ld_v, r, delta, update, seg_sq, x_out);
+int sddmm_update(cudaStream_t st, int64_t nnz, const int *rix, const int *col, const float *mval, float *y,
+                 const float *Us, int ld_us, const float *V, int ld_v, int r, float delta, int update, double *block_sq,
+                 float *x_out) {
+  MC_REQUIRE(r >= 0, "sddmm: negative rank");
+  MC_REQUIRE(ld_us % 4 == 0 && ld_v % 4 == 0 && ld_us >= r && ld_v >= r, "sddmm: bad leading dims");
+  const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSddmmBlocks, (nnz + kSddmmThreads - 1) / kSddmmThreads)));
+  sddmm_update_kernel<<<nb, kSddmmThreads, 0, st>>>(nnz, rix, col, mval, y, Us, ld_us, V, ld_v, (r + 3) / 4, delta,
+                                                     update, block_sq, x_out);
+  MC_CHECK_LAUNCH();
+  return nb;
+}
+
+int sddmm_partials() { return kSddmmBlocks; }
+
+void expand_rows(cudaStream_t st, int64_t m, const int *rp, int *rix) {
+  if (m <= 0) return;
+  const int64_t threads = m * 32;
+  expand_rows_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(m, rp, rix);
   MC_CHECK_LAUNCH();
 }
 

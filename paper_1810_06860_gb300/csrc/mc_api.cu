@@ -135,8 +135,8 @@ struct mc_handle_s {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   Alloc alloc;
-  // CSR
-  DBuf rp, ci, mval, y;
+  // CSR (rix: row of every entry)
+  DBuf rp, ci, mval, y, rix;
   // CSC
   DBuf cp, ri, perm, yc;
   SegPlan plan_r, plan_c;
@@ -229,12 +229,14 @@ double spmm_bytes(int64_t nnz, int64_t rows, int64_t rows_in, int K) {
 void spmm_Y(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_out) {
   fbuf(h, h->sp_part, (size_t)h->plan_r.nslot * K);
   Scope sc(h, MC_T_SPMM, spmm_bytes(h->nnz, h->m, h->n, K), 2.0 * h->nnz * K);
-  spmm(h->stream, h->plan_r, h->ci.as<int>(), h->y.as<float>(), X, ld_x, K, out, ld_out, h->sp_part.as<float>());
+  spmm(h->stream, h->plan_r, h->ci.as<int>(), h->y.as<float>(), h->n, X, ld_x, K, out, ld_out,
+       h->sp_part.as<float>());
 }
 void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_out) {
   fbuf(h, h->sp_part, (size_t)h->plan_c.nslot * K);
   Scope sc(h, MC_T_SPMM_T, spmm_bytes(h->nnz, h->n, h->m, K), 2.0 * h->nnz * K);
-  spmm(h->stream, h->plan_c, h->ri.as<int>(), h->yc.as<float>(), X, ld_x, K, out, ld_out, h->sp_part.as<float>());
+  spmm(h->stream, h->plan_c, h->ri.as<int>(), h->yc.as<float>(), h->m, X, ld_x, K, out, ld_out,
+       h->sp_part.as<float>());
 }
 
 void gram(mc_handle h, int64_t R, int K, const float *X, int ld, float *Gout, int ldg) {
@@ -616,17 +618,17 @@ mc_status svt_step(mc_handle h, mc_iter_info *out) {
     h->vb_ld = ldp;
   }
   // fused SDDMM + residual + update over Phi, then mirror Y into the CSC copy
-  double *sq = reinterpret_cast<double *>(fbuf(h, h->seg_sq, 2 * (size_t)h->plan_r.nseg + 16));
+  double *sq = reinterpret_cast<double *>(fbuf(h, h->seg_sq, 2 * (size_t)sddmm_partials() + 16));
+  int nsq = 0;
   {
-    Scope sc(h, MC_T_SDDMM, 16.0 * h->nnz + 4.0 * (h->m + 1) + 4.0 * (double)(h->m + h->n) * ldp,
-             2.0 * h->nnz * r);
-    sddmm_update(h->stream, h->plan_r, h->ci.as<int>(), h->mval.as<float>(), h->y.as<float>(), Us, ldp, Vr, ldp, r,
-                 (float)P.delta, 1, sq, nullptr);
+    Scope sc(h, MC_T_SDDMM, 20.0 * h->nnz + 4.0 * (double)(h->m + h->n) * ldp, 2.0 * h->nnz * r);
+    nsq = sddmm_update(h->stream, h->nnz, h->rix.as<int>(), h->ci.as<int>(), h->mval.as<float>(), h->y.as<float>(),
+                       Us, ldp, Vr, ldp, r, (float)P.delta, 1, sq, nullptr);
   }
   h->dsum.reserve(h->alloc, sizeof(double) * 1032);
   {
     Scope sc(h, MC_T_OTHER, 12.0 * h->nnz);
-    sum_doubles(h->stream, sq, h->plan_r.nseg, h->dsum.as<double>());
+    sum_doubles(h->stream, sq, nsq, h->dsum.as<double>());
     mirror_values(h->stream, h->nnz, h->perm.as<int>(), h->y.as<float>(), h->yc.as<float>());
   }
   double ssq = 0;
@@ -781,6 +783,8 @@ mc_status mc_create(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int
     MC_REQUIRE(!(fl[1] & 2), "columns must be strictly increasing within each row (sorted, no duplicates)");
     MC_REQUIRE(fl[2] == 0, "values must be finite");
     copy_in(s, h->y.p, h->mval.p, sizeof(float) * nnz);
+    h->rix.reserve(h->alloc, sizeof(int) * std::max<int64_t>(nnz, 1));
+    expand_rows(s, m, h->rp.as<int>(), h->rix.as<int>());
     // CSC copy
     h->cp.reserve(h->alloc, sizeof(int) * (n + 1));
     h->ri.reserve(h->alloc, sizeof(int) * std::max<int64_t>(nnz, 1));
@@ -810,12 +814,12 @@ void mc_destroy(mc_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   Alloc &a = h->alloc;
-  for (DBuf *b : {&h->rp, &h->ci, &h->mval, &h->y, &h->cp, &h->ri, &h->perm, &h->yc, &h->Om, &h->Q, &h->H, &h->Tmp,
+  for (DBuf *b : {&h->rp, &h->ci, &h->mval, &h->y, &h->rix, &h->cp, &h->ri, &h->perm, &h->yc, &h->Om, &h->Q, &h->H, &h->Tmp,
                   &h->T, &h->Bt, &h->G, &h->C, &h->Rinv, &h->lam, &h->W, &h->Wsel, &h->scale, &h->U, &h->V, &h->Ub,
                   &h->Vb, &h->seg_sq, &h->dsum, &h->tn_part, &h->sp_part, &h->eig_work, &h->flags})
     b->release(a);
   for (SegPlan *pl : {&h->plan_r, &h->plan_c})
-    for (DBuf *b : {&pl->seg_row, &pl->seg_beg, &pl->seg_end, &pl->seg_slot, &pl->split_row, &pl->split_slot})
+    for (DBuf *b : {&pl->seg, &pl->split_row, &pl->split_slot})
       b->release(a);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

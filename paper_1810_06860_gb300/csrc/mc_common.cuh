@@ -80,10 +80,7 @@ struct SegPlan {
   int64_t nseg = 0;      // number of segments (every row has >= 1, empty rows too)
   int64_t nsplit = 0;    // number of rows with > 1 segment
   int64_t nslot = 0;     // partial slots (segments of split rows)
-  DBuf seg_row;          // int32[nseg]  row of the segment
-  DBuf seg_beg;          // int32[nseg]  first entry
-  DBuf seg_end;          // int32[nseg]  one past the last entry
-  DBuf seg_slot;         // int32[nseg]  partial slot or -1 (direct write)
+  DBuf seg;              // int4[nseg]  (row, first entry, one past the last, partial slot or -1)
   DBuf split_row;        // int32[nsplit] rows with several segments
   DBuf split_slot;       // int32[nsplit+1] first slot of each split row
 };
@@ -108,19 +105,25 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
 // out (rows x K, ld_out) = A (CSR ptr/idx/val) * X (cols x K, ld_x).  K, ld_x,
 // ld_out multiples of 4 (padded columns must be zero in X).  partial must hold
 // plan.nslot * K floats.
-void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, const float *X,
-          int ld_x, int K, float *out, int ld_out, float *partial);
+// rows_in: rows of X (sizes the column chunks so the panel slice stays in L2).
+void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, int64_t rows_in,
+          const float *X, int ld_x, int K, float *out, int ld_out, float *partial);
 // y = P_Phi(M) scaled: y[e] = alpha * mval[e]
 void scale_values(cudaStream_t st, int64_t nnz, const float *src, float alpha, float *dst);
 // Yc[p] = Y[perm[p]]
 void mirror_values(cudaStream_t st, int64_t nnz, const int *perm, const float *y, float *yc);
 // Fused SVT update over Phi in CSR order (Alg. 6 steps 15-17):
 //   x_e = <Us[row_e, 0:r], V[col_e, 0:r]>,  res = M_e - x_e,
-//   partial sums of res^2 into seg_sq[nseg] (double),  y_e += delta * res
-//   (only if update != 0).  x_out (optional) receives x_e.
-void sddmm_update(cudaStream_t st, const SegPlan &plan, const int *col, const float *mval, float *y,
-                  const float *Us, int ld_us, const float *V, int ld_v, int r, float delta,
-                  int update, double *seg_sq, float *x_out);
+//   per-block sums of res^2 into block_sq (double, sddmm_partials() entries),
+//   y_e += delta * res (only if update != 0).  x_out (optional) receives x_e.
+//   Returns the number of block partials written.  Columns r..ld-1 of Us and
+//   V must be zero up to the next multiple of 4.
+int sddmm_update(cudaStream_t st, int64_t nnz, const int *rix, const int *col, const float *mval, float *y,
+                 const float *Us, int ld_us, const float *V, int ld_v, int r, float delta, int update,
+                 double *block_sq, float *x_out);
+int sddmm_partials();
+// rix[e] = row of CSR entry e.
+void expand_rows(cudaStream_t st, int64_t m, const int *rp, int *rix);
 // Deterministic sum of a double array into out[0] (one block, fixed order).
 void sum_doubles(cudaStream_t st, const double *in, int64_t count, double *out);
 // sum of squares of a float array, deterministic, into out[0] (double).
