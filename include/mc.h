@@ -210,6 +210,11 @@ mc_status mc_eig_sym(int K, int kw, const float *A, float *lam, float *W);
  * step of eigSVD (Alg. 3).  Host or device. */
 mc_status mc_gram(int64_t R, int K, const float *X, float *G);
 
+/* As mc_gram on the tensor cores (tcgen05, TF32 split into hi and lo parts
+ * for float32 accuracy); K <= 256.  Returns MC_ETIMEOUT if a bounded wait on
+ * a TMA or MMA barrier expired. */
+mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G);
+
 /* mc_gram_noalloc: G = X^T X (K x K, leading dimension ldg) of a tall device
  * matrix X (R rows, K columns, leading dimension ld, ld a multiple of 4), like
  * mc_gram but without allocating any device memory.  The paper has no

@@ -259,11 +259,11 @@ def eig_sym(A, kw: int):
     return lam, W
 
 
-def gram(X):
-    """X^T X of a tall float32 matrix."""
+def gram(X, tensor_cores: bool = False):
+    """X^T X of a tall float32 matrix (SIMT, or tcgen05 tensor cores for K <= 256)."""
     lib = load()
     X = np.ascontiguousarray(X, np.float32)
     G = np.empty((X.shape[1], X.shape[1]), np.float32)
-    _check(lib.mc_gram(X.shape[0], X.shape[1], X.ctypes.data_as(C.c_void_p), G.ctypes.data_as(C.c_void_p)),
-           "mc_gram")
+    fn = lib.mc_gram_tc if tensor_cores else lib.mc_gram
+    _check(fn(X.shape[0], X.shape[1], X.ctypes.data_as(C.c_void_p), G.ctypes.data_as(C.c_void_p)), fn.__name__)
     return G

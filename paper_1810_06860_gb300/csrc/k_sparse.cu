@@ -130,8 +130,10 @@ spmm_seg_kernel(int64_t nseg, const int4 *__restrict__ segs, const int *__restri
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int base = sd.y; base < sd.z; base += 32) {
     const int e = base + lane;
-    const int my_idx = e < sd.z ? idx[e] : 0;
-    const float my_val = e < sd.z ? val[e] : 0.f;
+    // indices and values are streamed once: evict-first, so the L1 keeps
+    // the gathered panel rows (popular columns are reused across rows)
+    const int my_idx = e < sd.z ? __ldcs(idx + e) : 0;
+    const float my_val = e < sd.z ? __ldcs(val + e) : 0.f;
     const int cnt = min(32, sd.z - base);
 #pragma unroll
     for (int t0 = 0; t0 < 32; t0 += G * U) {

@@ -1,0 +1,357 @@
+// Gram G = X^T X of a tall float32 panel (R x K, K <= 256) on the fifth-
+// generation tensor cores: the B = A^T A step of eigSVD (Alg. 3 step 1) and
+// the Gram of each CholeskyQR pass.
+//
+// One CTA of 128 threads per row range.  TMA loads 32-row stages of the panel
+// as 32-column boxes (128-byte rows, 128-byte swizzle) into a double-buffered
+// shared-memory ring.  The threads split every value into a TF32 "hi" part
+// (low 13 mantissa bits cleared) and the float32 remainder "lo" and write both
+// transposed into the K-major 128-byte-swizzled operand layout (the panel's
+// rows are the reduction dimension; a 32-row stage is exactly one 128-byte
+// swizzle row per panel column).  One thread issues tcgen05.mma kind::tf32 and
+// accumulates hi*hi + hi*lo + lo*hi into float32 accumulators in tensor
+// memory, which gives about float32 accuracy.
+// Up to K = 128 one 128 x N tile covers the Gram; above, a second 128-row tile
+// covers the remaining upper block.  Each CTA writes its partial Gram; a
+// reduction kernel adds the partials in a fixed order.  Every wait on an
+// mbarrier is bounded: on expiry the kernel records an error code and
+// finishes its outstanding work before it returns.
+#include "mc_common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace mc {
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_KT = 32;                 // panel rows per stage (4 MMA k-steps of 8)
+constexpr int TC_BOX_BYTES = 32 * TC_KT * 4;  // one 32-column box: 4 KiB
+constexpr int TC_MAX_BOXES = 8;           // K <= 256
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand in 128-byte-swizzled
+// atoms (8 rows of 128 bytes = 32 tf32 along K, 1024 bytes per atom): the
+// stride between 8-row groups is 1024 bytes; the leading offset is unused for
+// this layout.  A k-step of 8 elements advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused): 16 bytes
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride byte offset: 1024 bytes
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version for tcgen05
+  d |= static_cast<uint64_t>(2) << 61;  // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B tf32, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4)                                  // D format: f32
+         | (2u << 7)                                // A format: tf32
+         | (2u << 10)                               // B format: tf32
+         | (static_cast<uint32_t>(N >> 3) << 17)    // N / 8
+         | (static_cast<uint32_t>(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  // load and wait in one statement: the registers are defined only after the wait
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcSmem {
+  // 1024-byte aligned ring: raw / hi / lo, two stages each, boxes of 4 KiB
+  static constexpr size_t stage_bytes = (size_t)TC_MAX_BOXES * TC_BOX_BYTES;  // 32 KiB
+  static constexpr size_t total = 6 * stage_bytes + 1024;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int nbox, int two_tiles, int N0,
+               uint32_t tmem_cols, int64_t rows_per_cta, float *__restrict__ partial, int Kp, int *__restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t tc_raw_smem[];
+  __shared__ __align__(8) uint64_t full_bar[2];
+  __shared__ __align__(8) uint64_t mma_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int s_fail;
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_raw_smem) + 1023) & ~uintptr_t(1023));
+  uint8_t *raw[2] = {base, base + TcSmem::stage_bytes};
+  uint8_t *hi[2] = {base + 2 * TcSmem::stage_bytes, base + 3 * TcSmem::stage_bytes};
+  uint8_t *lo[2] = {base + 4 * TcSmem::stage_bytes, base + 5 * TcSmem::stage_bytes};
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int64_t r0 = blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(R, r0 + rows_per_cta);
+  const int S = r1 > r0 ? static_cast<int>((r1 - r0 + TC_KT - 1) / TC_KT) : 0;
+  const uint32_t stage_tx = static_cast<uint32_t>(nbox) * TC_BOX_BYTES;
+
+  if (tid == 0) {
+    mbar_init(&full_bar[0], 1);
+    mbar_init(&full_bar[1], 1);
+    mbar_init(&mma_bar[0], 1);
+    mbar_init(&mma_bar[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  auto issue_loads = [&](int s, int b) {
+    mbar_expect_tx(&full_bar[b], stage_tx);
+    const int y = static_cast<int>(r0 + (int64_t)s * TC_KT);
+    for (int j = 0; j < nbox; ++j) tma_load_2d(raw[b] + j * TC_BOX_BYTES, &xmap, 32 * j, y, &full_bar[b]);
+  };
+  if (tid == 0)
+    for (int s = 0; s < S && s < 2; ++s) issue_loads(s, s);
+
+  const uint32_t id0 = idesc_tf32(128, N0);
+  const uint32_t id1 = idesc_tf32(128, 128);
+  const int nvec = nbox * TC_BOX_BYTES / 16;  // float4 per stage
+  for (int s = 0; s < S; ++s) {
+    const int b = s & 1;
+    bool ok = mbar_wait(&full_bar[b], (s >> 1) & 1);
+    if (ok && s >= 2) ok = mbar_wait(&mma_bar[b], ((s - 2) >> 1) & 1);
+    if (!ok) atomicOr(&s_fail, 1);
+    // split into tf32 hi and float32 lo and transpose: the TMA tile holds
+    // element (r, c) (stage row r = reduction index, panel column c) at
+    //   box(c/32) * 4096 + r * 128 + (((c % 32) / 4) ^ (r % 8)) * 16 + (c % 4) * 4;
+    // the K-major operand stores it at
+    //   (c / 8) * 1024 + (c % 8) * 128 + ((r / 4) ^ (c % 8)) * 16 + (r % 4) * 4.
+    const float4 *src = reinterpret_cast<const float4 *>(raw[b]);
+    float *dh = reinterpret_cast<float *>(hi[b]);
+    float *dl = reinterpret_cast<float *>(lo[b]);
+    for (int q = tid; q < nvec; q += TC_THREADS) {
+      const int box = q >> 8, w = q & 255;  // 256 float4 per box
+      const int r = w >> 3, chunk = (w & 7) ^ (r & 7);
+      const int c0 = box * 32 + chunk * 4;
+      const float4 v = src[q];
+      const float vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u;
+        const int off = (c >> 3) * 256 + (c & 7) * 32 + ((((r >> 2) ^ (c & 7)) & 7) << 2) + (r & 3);
+        const float h = __uint_as_float(__float_as_uint(vals[u]) & 0xFFFFE000u);
+        dh[off] = h;
+        dl[off] = vals[u] - h;
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (s_fail) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ah = smem_u32(hi[b]), al = smem_u32(lo[b]);
+      for (int kg = 0; kg < TC_KT / 8; ++kg) {
+        const uint32_t ko = kg * 32;  // next 8 elements along K
+        const uint32_t acc0 = (s > 0 || kg > 0) ? 1u : 0u;
+        // tile 0: rows 0..127 of G (panel columns 0..127), columns 0..N0-1
+        mma_tf32(tmem, smem_desc(ah + ko), smem_desc(ah + ko), id0, acc0);
+        mma_tf32(tmem, smem_desc(ah + ko), smem_desc(al + ko), id0, 1u);
+        mma_tf32(tmem, smem_desc(al + ko), smem_desc(ah + ko), id0, 1u);
+        if (two_tiles) {
+          // tile 1: rows 128..255, columns 128..255 (16 atoms = 16 KiB further)
+          const uint32_t o1 = 16 * 1024 + ko;
+          const uint32_t d1 = tmem + static_cast<uint32_t>(N0);
+          mma_tf32(d1, smem_desc(ah + o1), smem_desc(ah + o1), id1, acc0);
+          mma_tf32(d1, smem_desc(ah + o1), smem_desc(al + o1), id1, 1u);
+          mma_tf32(d1, smem_desc(al + o1), smem_desc(ah + o1), id1, 1u);
+        }
+      }
+      mma_commit(&mma_bar[b]);
+      if (s + 2 < S) issue_loads(s + 2, b);
+    }
+  }
+  __syncthreads();
+  // wait for the last MMAs, then read the accumulators
+  bool have = S > 0 && !s_fail;
+  if (S > 0) {
+    const int sl = S - 1;
+    if (!mbar_wait(&mma_bar[sl & 1], (sl >> 1) & 1)) {
+      atomicOr(&s_fail, 2);
+      have = false;
+    }
+  }
+  // drain loads still in flight after an early exit
+  if (s_fail && tid == 0) {
+    for (int b = 0; b < 2; ++b) mbar_wait(&full_bar[b], 0), mbar_wait(&full_bar[b], 1);
+  }
+  __syncthreads();
+  tc_fence_after();
+  float *out = partial + (size_t)blockIdx.x * Kp * Kp;
+  const int row = 32 * wid + lane;  // accumulator lane = row within the tile
+  for (int tile = 0; tile < (two_tiles ? 2 : 1); ++tile) {
+    const int ncols = tile == 0 ? N0 : 128;
+    const int grow = tile * 128 + row;
+    const int gcol0 = tile * 128;
+    const uint32_t tcol = tile == 0 ? 0u : static_cast<uint32_t>(N0);
+    for (int c = 0; c < ncols; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + (static_cast<uint32_t>(32 * wid) << 16) + tcol + c, v);
+      if (grow < Kp) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int gc = gcol0 + c + i;
+          if (gc < Kp) out[(size_t)grow * Kp + gc] = have ? v[i] : 0.f;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  if (tid == 0 && s_fail && err) atomicOr(err, s_fail);
+}
+
+// G (K x K, ld_g) = sum of the partials.  Partial entries are valid in rows
+// 0..127 and in columns >= 128; the block rows >= 128, columns < 128 is read
+// transposed from rows < 128.
+__global__ void gram_tc_reduce_kernel(int K, int nsplit, const float *__restrict__ partial, int Kp,
+                                      float *__restrict__ G, int ld_g) {
+  const int64_t total = (int64_t)K * K;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int i = static_cast<int>(t / K), j = static_cast<int>(t % K);
+    int si = i, sj = j;
+    if (i >= 128 && j < 128) {
+      si = j;
+      sj = i;
+    }
+    const float *p = partial + (size_t)si * Kp + sj;
+    float acc = 0.f;
+    for (int s = 0; s < nsplit; ++s) acc += p[(size_t)s * Kp * Kp];
+    G[(int64_t)i * ld_g + j] = acc;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    MC_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    MC_REQUIRE(p != nullptr && q == cudaDriverEntryPointSuccess, "cuTensorMapEncodeTiled not available");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+int tc_nsplit(int64_t R) {
+  const int64_t by_rows = std::max<int64_t>(1, (R + 4 * TC_KT - 1) / (4 * TC_KT));
+  return static_cast<int>(std::min<int64_t>(152, by_rows));
+}
+
+}  // namespace
+
+size_t gram_tc_scratch_floats(int64_t R, int K) {
+  const int Kp = static_cast<int>(round_up(K, 32));
+  return (size_t)tc_nsplit(R) * Kp * Kp;
+}
+
+bool gram_tc_supported(int K, int ld, const void *X) {
+  return K >= 1 && K <= 256 && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+}
+
+void gram_tc(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *G, int ld_g, float *partial, int *err) {
+  MC_REQUIRE(gram_tc_supported(K, ld, X), "gram_tc: K must be <= 256, ld a multiple of 4, X 16-byte aligned");
+  MC_REQUIRE(R >= 1 && R < (int64_t(1) << 31), "gram_tc: row count out of range");
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(R)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  const cuuint32_t box[2] = {32, static_cast<cuuint32_t>(TC_KT)};
+  const cuuint32_t estride[2] = {1, 1};
+  const CUresult cr = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), gdim, gstride, box,
+                                  estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) fail(MC_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)cr));
+  const bool two = K > 128;
+  const int N0 = two ? 256 : std::max(32, static_cast<int>(round_up(K, 32)));
+  const int nbox = two ? 8 : 4;  // the A operand always spans 128 columns
+  uint32_t cols = 32;
+  while (cols < static_cast<uint32_t>(N0 + (two ? 128 : 0))) cols <<= 1;
+  const int Kp = static_cast<int>(round_up(K, 32));
+  const int nsplit = tc_nsplit(R);
+  const int64_t rows_per = round_up((R + nsplit - 1) / nsplit, TC_KT);
+  const size_t smem = TcSmem::total;
+  MC_CUDA(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  gram_tc_kernel<<<nsplit, TC_THREADS, smem, st>>>(map, R, K, nbox, two ? 1 : 0, N0, cols, rows_per, partial, Kp, err);
+  MC_CHECK_LAUNCH();
+  const int64_t total = (int64_t)K * K;
+  const int nb = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 4));
+  gram_tc_reduce_kernel<<<nb, 256, 0, st>>>(K, nsplit, partial, Kp, G, ld_g);
+  MC_CHECK_LAUNCH();
+}
+
+}  // namespace mc

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <memory>
@@ -239,9 +240,24 @@ void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_ou
        h->sp_part.as<float>());
 }
 
+// Gram X^T X: the tensor-core kernel (tcgen05, 3xTF32) for 32 <= K <= 256,
+// SIMT otherwise; MC_GRAM_SIMT=1 selects SIMT everywhere.
+bool use_tensor_gram() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_GRAM_SIMT");
+    return !(v && v[0] == '1');
+  }();
+  return on;
+}
+
 void gram(mc_handle h, int64_t R, int K, const float *X, int ld, float *Gout, int ldg) {
-  fbuf(h, h->tn_part, gemm_tn_scratch_floats(R, K, K));
   Scope sc(h, MC_T_GRAM, 4.0 * R * K + 4.0 * K * K, 1.0 * R * K * (K + 1));
+  if (use_tensor_gram() && K >= 32 && gram_tc_supported(K, ld, X)) {
+    fbuf(h, h->tn_part, gram_tc_scratch_floats(R, K));
+    gram_tc(h->stream, R, K, X, ld, Gout, ldg, h->tn_part.as<float>(), h->flags.as<int>() + 3);
+    return;
+  }
+  fbuf(h, h->tn_part, gemm_tn_scratch_floats(R, K, K));
   gemm_tn(h->stream, R, K, K, X, ld, X, ld, Gout, ldg, true, h->tn_part.as<float>());
 }
 
@@ -356,7 +372,10 @@ void ritz(mc_handle h, const float *Qb, int ldq, int Kq, int kw) {
   }
   h->h_lam.assign(kw, 0.f);
   MC_CUDA(cudaMemcpyAsync(h->h_lam.data(), lam, sizeof(float) * kw, cudaMemcpyDeviceToHost, h->stream));
+  int werr = 0;
+  MC_CUDA(cudaMemcpyAsync(&werr, h->flags.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   sync(h);
+  if (werr) fail(MC_ETIMEOUT, "a bounded wait in the tensor-core Gram expired (code " + std::to_string(werr) + ")");
   h->Kq = Kq;
   h->kw = kw;
 }
@@ -1007,6 +1026,32 @@ mc_status mc_eig_sym(int K, int kw, const float *A, float *lam, float *W) {
     cudaFree(dl);
     cudaFree(dW);
     cudaFree(work);
+    return MC_OK;
+  });
+}
+
+mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G) {
+  if (R < 1 || K < 1 || K > 256 || !X || !G) return MC_EINVAL;
+  return guarded([&]() -> mc_status {
+    const int kp = (int)round_up(K, 4);
+    float *dX = nullptr, *dG = nullptr, *part = nullptr;
+    int *derr = nullptr;
+    MC_CUDA(cudaMalloc(&dX, sizeof(float) * R * kp));
+    MC_CUDA(cudaMalloc(&dG, sizeof(float) * K * K));
+    MC_CUDA(cudaMalloc(&part, sizeof(float) * gram_tc_scratch_floats(R, K)));
+    MC_CUDA(cudaMalloc(&derr, sizeof(int)));
+    MC_CUDA(cudaMemset(derr, 0, sizeof(int)));
+    MC_CUDA(cudaMemset(dX, 0, sizeof(float) * R * kp));
+    MC_CUDA(cudaMemcpy2D(dX, sizeof(float) * kp, X, sizeof(float) * K, sizeof(float) * K, R, cudaMemcpyDefault));
+    gram_tc(0, R, K, dX, kp, dG, K, part, derr);
+    int herr = 0;
+    MC_CUDA(cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost));
+    MC_CUDA(cudaMemcpy(G, dG, sizeof(float) * K * K, cudaMemcpyDefault));
+    cudaFree(dX);
+    cudaFree(dG);
+    cudaFree(part);
+    cudaFree(derr);
+    if (herr) fail(MC_ETIMEOUT, "a bounded wait in the tensor-core Gram expired");
     return MC_OK;
   });
 }

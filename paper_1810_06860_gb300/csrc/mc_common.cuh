@@ -156,6 +156,12 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
 // out[c] = sum_r X[r][c]^2 (deterministic).  scratch: colsumsq_scratch_floats(K).
 size_t colsumsq_scratch_floats(int K);
 void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *out, float *scratch);
+// Gram on the tensor cores (k_tc.cu): G = X^T X for K <= 256, ld % 4 == 0,
+// X 16-byte aligned.  partial: gram_tc_scratch_floats(R, K) floats.  err
+// (device int, may be NULL) receives a nonzero code if a bounded wait expired.
+size_t gram_tc_scratch_floats(int64_t R, int K);
+bool gram_tc_supported(int K, int ld, const void *X);
+void gram_tc(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *G, int ld_g, float *partial, int *err);
 // Top-kw eigenpairs of the symmetric K x K matrix A (lower triangle read).
 // lam: kw floats descending; W: K x kw (ld_w).  work: eig_work_bytes(K, kw).
 size_t eig_work_bytes(int K, int kw);

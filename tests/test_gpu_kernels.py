@@ -135,3 +135,16 @@ def test_csc_copy_matches_transpose(mc):
         A = sp.csr_matrix((o.val.astype(np.float64), o.col, o.row_ptr), shape=(o.m, o.n))
         got = h.spmm(Xt, trans=True)
         assert np.max(np.abs(got - A.T @ Xt.astype(np.float64))) < 1e-4 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("R,K", [(1, 32), (37, 60), (1000, 64), (5000, 100), (3000, 128), (2000, 129),
+                                 (20000, 200), (138000, 240), (777, 256)])
+def test_gram_tensor_cores(mc, R, K):
+    rng = np.random.default_rng(R * 3 + K)
+    X = rng.standard_normal((R, K)).astype(np.float32)
+    X[:, ::7] *= 30.0  # uneven column scales
+    G = mc.gram(X, tensor_cores=True)
+    ref = X.astype(np.float64).T @ X.astype(np.float64)
+    # three TF32 products: about float32 accuracy relative to the entries' scale
+    scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    assert np.max(np.abs(G - ref) / scale) < 2e-5
