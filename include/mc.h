@@ -73,7 +73,7 @@ typedef struct {
   int q_reuse;    /* recycled SVD calls per subspace (10) */
   int recycle;    /* 0 none, 1 reuse Q, 2 reuse U (Sec. IV.B), 3 warm-start Omega with V */
   int k_max;      /* cap on the SVD rank (0 = min(m,n) - s) */
-  int precision;  /* 0 plain FP32 */
+  int precision;  /* 0 plain float32, 1 bf16 panels in the Krylov products */
   uint64_t seed;  /* key of the Philox stream that draws Omega */
 } mc_params;
 
@@ -125,6 +125,14 @@ mc_status mc_set_values(mc_handle h, const float *val);
  * has lower rank).  Buffers must hold k columns. */
 mc_status mc_rsvd_bki(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U,
                       float *S, float *V, int *k_out);
+
+/* Precision of the randomized SVDs of this handle: 0 plain float32 (default);
+ * 1 mixed: the panels that feed the Krylov / power products (Omega, A^T Q and
+ * Q) are read as bf16 with float32 sums, the basis is orthonormalised in
+ * float32, and the final projection B^T = Y^T Q uses the float32 basis (one
+ * float32 pass over the Krylov block).  mc_svt_step sets it from
+ * params->precision.  MC_EINVAL for other values. */
+mc_status mc_set_precision(mc_handle h, int precision);
 
 /* mc_rsvd_pi: as mc_rsvd_bki but by rSVD-PI (Alg. 4): p power steps with a
  * block normalisation between them, eigSVD of the last block, B^T = Y^T Q. */

@@ -146,6 +146,10 @@ class Handle:
     def __exit__(self, *a):
         self.close()
 
+    def set_precision(self, precision: int):
+        """0: plain float32; 1: bf16 panels in the Krylov products (mixed form)."""
+        _check(self._lib.mc_set_precision(self._h, int(precision)), "mc_set_precision")
+
     # ---- randomized SVDs -------------------------------------------------
     def _rsvd(self, fn, k, s, p, seed, call_id, device):
         U = _out((self.m, k), np.float32, device)

@@ -173,6 +173,85 @@ gemm_nn_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x,
   }
 }
 
+// ===================================================== chol_inv (one warp) ==
+// K <= 64: the same factorisation and inverse by a single warp (no block
+// barriers).  Lane l owns rows l and l + 32 of the working matrices.
+__global__ void __launch_bounds__(32)
+chol_inv_warp_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
+                     float ref_tol, float *__restrict__ Rinv) {
+  __shared__ float L[64][65];
+  __shared__ float X[64][65];
+  __shared__ float keepf[64];
+  const int lane = threadIdx.x;
+  float tr = 0.f, mx = 0.f;
+  for (int i = lane; i < K; i += 32) {
+    const float gi = G[(int64_t)i * ld + i];
+    tr += gi;
+    mx = fmaxf(mx, gi);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, off);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  const float shift = shift_rel * tr / K;
+  const float drop = fmaxf(1e-30f, 1e-12f * mx) + shift;
+  for (int i = lane; i < K; i += 32)
+    keepf[i] = (ref_diag && !(G[(int64_t)i * ld + i] > ref_tol * ref_diag[i])) ? 0.f : 1.f;
+  __syncwarp();
+  for (int i = 0; i < K; ++i)
+    for (int j = lane; j < K; j += 32) {
+      const bool live = keepf[i] != 0.f && keepf[j] != 0.f;
+      L[i][j] = (j <= i && live) ? G[(int64_t)i * ld + j] + (i == j ? shift : 0.f) : 0.f;
+    }
+  __syncwarp();
+  for (int j = 0; j < K; ++j) {
+    const float d = L[j][j];
+    const bool keep = d > drop;
+    const float inv = keep ? rsqrtf(d) : 0.f;
+    __syncwarp();
+    for (int i = j + 1 + lane; i < K; i += 32) L[i][j] *= inv;
+    if (lane == 0) {
+      L[j][j] = keep ? d * inv : 1.0f;
+      if (!keep) keepf[j] = 0.f;
+    }
+    __syncwarp();
+    if (keep) {
+      // trailing update, the lanes spread over the rows' entries
+      for (int a = j + 1; a < K; ++a) {
+        const float la = L[a][j];
+        for (int b = j + 1 + lane; b <= a; b += 32) L[a][b] -= la * L[b][j];
+      }
+      __syncwarp();
+    }
+  }
+  // forward substitution, lane l solves columns l and l + 32; four partial
+  // sums shorten the dependency chain
+  for (int c = lane; c < K; c += 32) {
+    const bool kc = keepf[c] != 0.f;
+    for (int i = 0; i < K; ++i) {
+      float x = 0.f;
+      if (kc && i >= c && keepf[i] != 0.f) {
+        float a0 = (i == c) ? 1.0f : 0.0f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int l = c;
+        for (; l + 3 < i; l += 4) {
+          a0 -= L[i][l] * X[l][c];
+          a1 -= L[i][l + 1] * X[l + 1][c];
+          a2 -= L[i][l + 2] * X[l + 2][c];
+          a3 -= L[i][l + 3] * X[l + 3][c];
+        }
+        for (; l < i; ++l) a0 -= L[i][l] * X[l][c];
+        x = ((a0 + a1) + (a2 + a3)) / L[i][i];
+      }
+      X[i][c] = x;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < K * K; t += 32) {
+    const int i = t / K, j = t % K;
+    Rinv[t] = X[j][i];
+  }
+}
+
 // =========================================================== chol_inv ======
 // One block.  G + shift I = L L^T (right-looking, warp per row of the trailing
 // update); pivots below the drop threshold make their column "absent": its
@@ -243,9 +322,16 @@ chol_inv_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, con
     for (int i = 0; i < K; ++i) {
       float x = 0.f;
       if (kc && i >= c && flags[i] != 0.f) {
-        float acc = (i == c) ? 1.0f : 0.0f;
-        for (int l = c; l < i; ++l) acc -= L[i * K + l] * X[(int64_t)l * K + c];
-        x = acc / L[i * K + i];
+        float a0 = (i == c) ? 1.0f : 0.0f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int l = c;
+        for (; l + 3 < i; l += 4) {
+          a0 -= L[i * K + l] * X[(int64_t)l * K + c];
+          a1 -= L[i * K + l + 1] * X[(int64_t)(l + 1) * K + c];
+          a2 -= L[i * K + l + 2] * X[(int64_t)(l + 2) * K + c];
+          a3 -= L[i * K + l + 3] * X[(int64_t)(l + 3) * K + c];
+        }
+        for (; l < i; ++l) a0 -= L[i * K + l] * X[(int64_t)l * K + c];
+        x = ((a0 + a1) + (a2 + a3)) / L[i * K + i];
       }
       X[(int64_t)i * K + c] = x;
     }
@@ -282,12 +368,19 @@ __global__ void colsumsq_partial_kernel(int64_t R, int K, const float *__restric
   }
 }
 
+// One block per column: a fixed-order tree over the chunk partials.
 __global__ void colsumsq_reduce_kernel(int K, int nchunk, const float *__restrict__ part, float *__restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int b = 0; b < nchunk; ++b) acc += part[(int64_t)b * K + c];
-    out[c] = acc;
+  __shared__ float sh[256];
+  const int c = blockIdx.x;
+  float acc = 0.f;
+  for (int b = threadIdx.x; b < nchunk; b += blockDim.x) acc += part[(int64_t)b * K + c];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < (unsigned)off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) out[c] = sh[0];
 }
 
 // out (K x ncp) = W[:, 0:ncols] with zero columns up to ncp
@@ -311,7 +404,7 @@ void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *
   const int64_t rows_per = (R + nchunk - 1) / nchunk;
   colsumsq_partial_kernel<<<nchunk, 128, 0, st>>>(R, K, X, ld, rows_per, scratch);
   MC_CHECK_LAUNCH();
-  colsumsq_reduce_kernel<<<(K + 127) / 128, 128, 0, st>>>(K, nchunk, scratch, out);
+  colsumsq_reduce_kernel<<<K, 256, 0, st>>>(K, nchunk, scratch, out);
   MC_CHECK_LAUNCH();
 }
 
@@ -364,6 +457,11 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag, float ref_tol,
               float *Rinv) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
+  if (K <= 64) {
+    chol_inv_warp_kernel<<<1, 32, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv);
+    MC_CHECK_LAUNCH();
+    return;
+  }
   const size_t base = sizeof(float) * ((size_t)K * K + K);
   MC_REQUIRE(base <= 220 * 1024, "chol_inv: block too wide for shared memory");
   const bool x_sm = base + sizeof(float) * (size_t)K * K <= 220 * 1024;

@@ -13,6 +13,8 @@
 // atomics touch floating-point data.
 #include "mc_common.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -168,6 +170,76 @@ spmm_seg_kernel(int64_t nseg, const int4 *__restrict__ segs, const int *__restri
   float4 *dst = sd.w < 0 ? reinterpret_cast<float4 *>(out + (int64_t)sd.x * ld_out)
                          : reinterpret_cast<float4 *>(partial + (int64_t)sd.w * (K4 * 4));
   dst[li] = acc;
+}
+
+// Same work split with a BF16 panel (mixed-precision form): a lane owns 8
+// consecutive columns (one 16-byte load of 8 bf16) and accumulates in float32.
+template <int G>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+spmm_seg_bf16_kernel(int64_t nseg, const int4 *__restrict__ segs, const int *__restrict__ idx,
+                     const float *__restrict__ val, const __nv_bfloat16 *__restrict__ X, int ld_x, int K8,
+                     float *__restrict__ out, int ld_out, float *__restrict__ partial) {
+  constexpr int L = 32 / G;
+  constexpr int U = G >= 8 ? 1 : (G >= 2 ? 2 : 4);
+  const int lane = threadIdx.x & 31;
+  const int64_t seg = blockIdx.x * (int64_t)kWarpsPerBlock + (threadIdx.x >> 5);
+  if (seg >= nseg) return;
+  const int g = lane / L, li = lane % L;
+  const int4 sd = segs[seg];
+  const bool active = li < K8;
+  float acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+  for (int base = sd.y; base < sd.z; base += 32) {
+    const int e = base + lane;
+    const int my_idx = e < sd.z ? __ldcs(idx + e) : 0;
+    const float my_val = e < sd.z ? __ldcs(val + e) : 0.f;
+    const int cnt = min(32, sd.z - base);
+#pragma unroll
+    for (int t0 = 0; t0 < 32; t0 += G * U) {
+      if (t0 >= cnt) break;  // warp-uniform
+      uint4 xv[U];
+      float av[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int src = t0 + u * G + g;
+        const int j = __shfl_sync(0xffffffffu, my_idx, src);
+        av[u] = __shfl_sync(0xffffffffu, my_val, src);
+        xv[u] = make_uint4(0u, 0u, 0u, 0u);
+        if (active && src < cnt) xv[u] = __ldg(reinterpret_cast<const uint4 *>(X + (int64_t)j * ld_x) + li);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t w[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float lo = __uint_as_float(w[q] << 16), hi = __uint_as_float(w[q] & 0xFFFF0000u);
+          acc[2 * q] = fmaf(av[u], lo, acc[2 * q]);
+          acc[2 * q + 1] = fmaf(av[u], hi, acc[2 * q + 1]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+  if (g != 0 || !active) return;
+  float *dst = sd.w < 0 ? out + (int64_t)sd.x * ld_out : partial + (int64_t)sd.w * (K8 * 8);
+  float4 *d4 = reinterpret_cast<float4 *>(dst + li * 8);
+  d4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  d4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+}
+
+// Round a float32 panel to bf16 (nearest even); columns cols..ld_out-1 zero.
+__global__ void to_bf16_kernel(int64_t rows, int cols, const float *__restrict__ in, int ld_in,
+                               __nv_bfloat16 *__restrict__ out, int ld_out) {
+  const int64_t total = rows * ld_out;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / ld_out;
+    const int c = static_cast<int>(t - r * ld_out);
+    out[t] = __float2bfloat16_rn(c < cols ? in[r * ld_in + c] : 0.f);
+  }
 }
 
 __global__ void spmm_fixup_kernel(int64_t nsplit, const int *__restrict__ split_row,
@@ -403,6 +475,7 @@ void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val
 #define MC_SPMM_ARGS plan.nseg, plan.seg.as<int4>(), idx, val, X + c0, ld_x, K4, out + c0, ld_out, partial
     if (K4 <= 2) spmm_seg_kernel<16><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
     else if (K4 <= 4) spmm_seg_kernel<8><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+
     else if (K4 <= 8) spmm_seg_kernel<4><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
     else if (K4 <= 16) spmm_seg_kernel<2><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
     else spmm_seg_kernel<1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
@@ -414,6 +487,38 @@ void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val
       MC_CHECK_LAUNCH();
     }
   }
+}
+
+void spmm_bf16(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, const void *Xbf, int ld_x,
+               int K, float *out, int ld_out, float *partial) {
+  if (plan.nseg == 0 || K <= 0) return;
+  MC_REQUIRE(K % 8 == 0 && ld_x % 8 == 0 && ld_out % 4 == 0 && K <= 256, "spmm_bf16: K and ld must be multiples of 8, K <= 256");
+  const __nv_bfloat16 *X = static_cast<const __nv_bfloat16 *>(Xbf);
+  const int K8 = K / 8;
+  const int64_t blocks = (plan.nseg + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int threads = kWarpsPerBlock * 32;
+#define MC_BF_ARGS plan.nseg, plan.seg.as<int4>(), idx, val, X, ld_x, K8, out, ld_out, partial
+  if (K8 <= 1) spmm_seg_bf16_kernel<32><<<blocks, threads, 0, st>>>(MC_BF_ARGS);
+  else if (K8 <= 2) spmm_seg_bf16_kernel<16><<<blocks, threads, 0, st>>>(MC_BF_ARGS);
+  else if (K8 <= 4) spmm_seg_bf16_kernel<8><<<blocks, threads, 0, st>>>(MC_BF_ARGS);
+  else if (K8 <= 8) spmm_seg_bf16_kernel<4><<<blocks, threads, 0, st>>>(MC_BF_ARGS);
+  else if (K8 <= 16) spmm_seg_bf16_kernel<2><<<blocks, threads, 0, st>>>(MC_BF_ARGS);
+  else spmm_seg_bf16_kernel<1><<<blocks, threads, 0, st>>>(MC_BF_ARGS);
+#undef MC_BF_ARGS
+  MC_CHECK_LAUNCH();
+  if (plan.nsplit > 0) {
+    spmm_fixup_kernel<<<static_cast<unsigned>(plan.nsplit), 128, 0, st>>>(
+        plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, K, out, ld_out);
+    MC_CHECK_LAUNCH();
+  }
+}
+
+void to_bf16(cudaStream_t st, int64_t rows, int cols, const float *in, int ld_in, void *out, int ld_out) {
+  const int64_t total = rows * ld_out;
+  if (total <= 0) return;
+  to_bf16_kernel<<<grid_for(total, 256), 256, 0, st>>>(rows, cols, in, ld_in, static_cast<__nv_bfloat16 *>(out),
+                                                       ld_out);
+  MC_CHECK_LAUNCH();
 }
 
 void scale_values(cudaStream_t st, int64_t nnz, const float *src, float alpha, float *dst) {

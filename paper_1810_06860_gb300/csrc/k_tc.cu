@@ -277,20 +277,36 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
 // G (K x K, ld_g) = sum of the partials.  Partial entries are valid in rows
 // 0..127 and in columns >= 128; the block rows >= 128, columns < 128 is read
 // transposed from rows < 128.
-__global__ void gram_tc_reduce_kernel(int K, int nsplit, const float *__restrict__ partial, int Kp,
-                                      float *__restrict__ G, int ld_g) {
+__global__ void __launch_bounds__(256)
+gram_tc_reduce_kernel(int K, int nsplit, const float *__restrict__ partial, int Kp, float *__restrict__ G, int ld_g) {
+  // a block covers 32 outputs with 8 lanes of split groups each (fixed order)
+  __shared__ float sh[8][33];
   const int64_t total = (int64_t)K * K;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    int i = static_cast<int>(t / K), j = static_cast<int>(t % K);
-    int si = i, sj = j;
-    if (i >= 128 && j < 128) {
-      si = j;
-      sj = i;
-    }
-    const float *p = partial + (size_t)si * Kp + sj;
+  const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+  for (int64_t base = (int64_t)blockIdx.x * 32; base < total; base += (int64_t)gridDim.x * 32) {
+    const int64_t t = base + o;
     float acc = 0.f;
-    for (int s = 0; s < nsplit; ++s) acc += p[(size_t)s * Kp * Kp];
-    G[(int64_t)i * ld_g + j] = acc;
+    int i = 0, j = 0;
+    if (t < total) {
+      i = static_cast<int>(t / K);
+      j = static_cast<int>(t % K);
+      int si = i, sj = j;
+      if (i >= 128 && j < 128) {
+        si = j;
+        sj = i;
+      }
+      const float *p = partial + (size_t)si * Kp + sj;
+      for (int sp = g; sp < nsplit; sp += 8) acc += p[(size_t)sp * Kp * Kp];
+    }
+    sh[g][o] = acc;
+    __syncthreads();
+    if (g == 0 && t < total) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += sh[q][o];
+      G[(int64_t)i * ld_g + j] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -349,7 +365,7 @@ void gram_tc(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *G
   gram_tc_kernel<<<nsplit, TC_THREADS, smem, st>>>(map, R, K, nbox, two ? 1 : 0, N0, cols, rows_per, partial, Kp, err);
   MC_CHECK_LAUNCH();
   const int64_t total = (int64_t)K * K;
-  const int nb = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 4));
+  const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
   gram_tc_reduce_kernel<<<nb, 256, 0, st>>>(K, nsplit, partial, Kp, G, ld_g);
   MC_CHECK_LAUNCH();
 }

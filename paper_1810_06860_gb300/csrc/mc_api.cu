@@ -143,6 +143,8 @@ struct mc_handle_s {
   SegPlan plan_r, plan_c;
   // panels
   DBuf Om, Q, H, Tmp, T, Bt, G, C, Rinv, lam, W, Wsel, scale, U, V, Ub, Vb, seg_sq, dsum, tn_part, sp_part, eig_work;
+  DBuf Om_bf, Q_bf, T_bf;  // bf16 panels of the mixed-precision form
+  int precision = 0;       // 0 plain float32, 1 bf16 panels in the Krylov products
   DBuf flags;
   // rSVD result bookkeeping
   int Kq = 0;          // columns of the basis whose Ritz pairs are in W (incl. zero padding)
@@ -188,6 +190,9 @@ float *fbuf(mc_handle h, DBuf &b, size_t count) {
   return b.as<float>();
 }
 
+// Krylov blocks are padded with zero columns to 4 (plain) or 8 (bf16 panels).
+int block_align(mc_handle h) { return h->precision ? 8 : 4; }
+
 // clamp as the oracle does: one block must fit, (p+1)(k+s) <= min(m, n), and
 // the basis width (blocks padded to 4 columns) stays within kMaxKt.
 void clamp_kp(mc_handle h, int s, int &k, int &p) {
@@ -195,7 +200,7 @@ void clamp_kp(mc_handle h, int s, int &k, int &p) {
   if (k + s > lim) k = std::max<int64_t>(1, lim - s);
   MC_REQUIRE(k + s <= lim, "k + s exceeds min(m, n)");
   const int kb = k + s;
-  const int kbp = (int)round_up(kb, 4);
+  const int kbp = (int)round_up(kb, block_align(h));
   MC_REQUIRE(kbp <= kMaxKt, "k + s above the supported basis width (1024)");
   p = (int)std::max<int64_t>(0, std::min<int64_t>(p, lim / kb - 1));
   p = std::max(0, std::min(p, kMaxKt / kbp - 1));
@@ -233,6 +238,24 @@ void spmm_Y(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_out
   spmm(h->stream, h->plan_r, h->ci.as<int>(), h->y.as<float>(), h->n, X, ld_x, K, out, ld_out,
        h->sp_part.as<float>());
 }
+// Products with bf16 panels (mixed-precision form); X has ld_x = K columns.
+void spmm_Y_bf(mc_handle h, const void *X, int K, float *out, int ld_out) {
+  fbuf(h, h->sp_part, (size_t)h->plan_r.nslot * K);
+  Scope sc(h, MC_T_SPMM, 8.0 * h->nnz + 4.0 * (h->m + 1) + (2.0 * h->n + 4.0 * h->m) * K, 2.0 * h->nnz * K);
+  spmm_bf16(h->stream, h->plan_r, h->ci.as<int>(), h->y.as<float>(), X, K, K, out, ld_out, h->sp_part.as<float>());
+}
+void spmm_Yt_bf(mc_handle h, const void *X, int K, float *out, int ld_out) {
+  fbuf(h, h->sp_part, (size_t)h->plan_c.nslot * K);
+  Scope sc(h, MC_T_SPMM_T, 8.0 * h->nnz + 4.0 * (h->n + 1) + (2.0 * h->m + 4.0 * h->n) * K, 2.0 * h->nnz * K);
+  spmm_bf16(h->stream, h->plan_c, h->ri.as<int>(), h->yc.as<float>(), X, K, K, out, ld_out, h->sp_part.as<float>());
+}
+void *bf_panel(mc_handle h, DBuf &b, int64_t rows, int cols, const float *src, int ld_src) {
+  b.reserve(h->alloc, 2 * (size_t)std::max<int64_t>(rows * cols, 1));
+  Scope sc(h, MC_T_OTHER, 6.0 * rows * cols);
+  to_bf16(h->stream, rows, cols, src, ld_src, b.p, cols);
+  return b.p;
+}
+
 void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_out) {
   fbuf(h, h->sp_part, (size_t)h->plan_c.nslot * K);
   Scope sc(h, MC_T_SPMM_T, spmm_bytes(h->nnz, h->n, h->m, K), 2.0 * h->nnz * K);
@@ -240,8 +263,8 @@ void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_ou
        h->sp_part.as<float>());
 }
 
-// Gram X^T X: the tensor-core kernel (tcgen05, 3xTF32) for 32 <= K <= 256,
-// SIMT otherwise; MC_GRAM_SIMT=1 selects SIMT everywhere.
+// Gram X^T X: the tensor-core kernel (tcgen05, 3xTF32) for tc_min_k() <= K
+// <= 256, SIMT otherwise; MC_GRAM_SIMT=1 selects SIMT everywhere.
 bool use_tensor_gram() {
   static const bool on = [] {
     const char *v = std::getenv("MC_GRAM_SIMT");
@@ -250,9 +273,17 @@ bool use_tensor_gram() {
   return on;
 }
 
+int tc_min_k() {
+  static const int v = [] {
+    const char *e = std::getenv("MC_GRAM_TC_MIN_K");
+    return e ? std::max(1, std::atoi(e)) : 32;
+  }();
+  return v;
+}
+
 void gram(mc_handle h, int64_t R, int K, const float *X, int ld, float *Gout, int ldg) {
   Scope sc(h, MC_T_GRAM, 4.0 * R * K + 4.0 * K * K, 1.0 * R * K * (K + 1));
-  if (use_tensor_gram() && K >= 32 && gram_tc_supported(K, ld, X)) {
+  if (use_tensor_gram() && K >= tc_min_k() && gram_tc_supported(K, ld, X)) {
     fbuf(h, h->tn_part, gram_tc_scratch_floats(R, K));
     gram_tc(h->stream, R, K, X, ld, Gout, ldg, h->tn_part.as<float>(), h->flags.as<int>() + 3);
     return;
@@ -314,19 +345,29 @@ void draw_omega(mc_handle h, int kb, int kbp, uint64_t seed, uint64_t call_id, c
 }
 
 // Block-Krylov basis of Alg. 5 (steps 1-7) into h->Q (m x (p+1)*kbp).
+// With the mixed-precision form the three panels that feed the Krylov
+// products (Omega, A^T Q_{i-1} and Q_{i-1}) are read as bf16; sums stay
+// float32 and the basis is orthonormalised in float32.
 void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, const float *warm, int warm_ld,
                 int warm_cols) {
-  const int kbp = (int)round_up(kb, 4);
+  const bool mixed = h->precision != 0;
+  const int kbp = (int)round_up(kb, block_align(h));
   const int ktp = (p + 1) * kbp;
   draw_omega(h, kb, kbp, seed, call_id, warm, warm_ld, warm_cols);
   float *Q = fbuf(h, h->Q, (size_t)h->m * ktp);
   float *H = fbuf(h, h->H, (size_t)h->m * kbp);
   float *T = fbuf(h, h->T, (size_t)h->n * kbp);
-  spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // H_0 = A Omega
+  if (mixed) spmm_Y_bf(h, bf_panel(h, h->Om_bf, h->n, kbp, h->Om.as<float>(), kbp), kbp, H, kbp);
+  else spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // H_0 = A Omega
   orth_block(h, h->m, kbp, H, kbp, Q, ktp);
   for (int i = 1; i <= p; ++i) {
-    spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, T, kbp);  // A^T Q_{i-1}
-    spmm_Y(h, T, kbp, kbp, H, kbp);                          // A (A^T Q_{i-1})
+    if (mixed) {
+      spmm_Yt_bf(h, bf_panel(h, h->Q_bf, h->m, kbp, Q + (size_t)(i - 1) * kbp, ktp), kbp, T, kbp);
+      spmm_Y_bf(h, bf_panel(h, h->T_bf, h->n, kbp, T, kbp), kbp, H, kbp);
+    } else {
+      spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, T, kbp);  // A^T Q_{i-1}
+      spmm_Y(h, T, kbp, kbp, H, kbp);                          // A (A^T Q_{i-1})
+    }
     float *ref = fbuf(h, h->lam, (size_t)kbp + colsumsq_scratch_floats(kbp));
     colsumsq(h->stream, h->m, kbp, H, kbp, ref, ref + kbp);
     project_out(h, h->m, Q, ktp, i * kbp, H, kbp, kbp);
@@ -338,16 +379,23 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
 
 // Power-iteration basis of Alg. 4 (steps 1-7) into h->Q (m x kbp).
 void power_pi(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id) {
-  const int kbp = (int)round_up(kb, 4);
+  const bool mixed = h->precision != 0;
+  const int kbp = (int)round_up(kb, block_align(h));
   draw_omega(h, kb, kbp, seed, call_id, nullptr, 0, 0);
   float *Q = fbuf(h, h->Q, (size_t)h->m * kbp);
   float *H = fbuf(h, h->H, (size_t)h->m * kbp);
   float *T = fbuf(h, h->T, (size_t)h->n * kbp);
-  spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // Q = A Omega
+  if (mixed) spmm_Y_bf(h, bf_panel(h, h->Om_bf, h->n, kbp, h->Om.as<float>(), kbp), kbp, H, kbp);
+  else spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // Q = A Omega
   for (int i = 0; i < p; ++i) {
     orth_block(h, h->m, kbp, H, kbp, Q, kbp);      // lu(Q), an orthonormal basis of the same range
-    spmm_Yt(h, Q, kbp, kbp, T, kbp);
-    spmm_Y(h, T, kbp, kbp, H, kbp);                // Q = A (A^T Q)
+    if (mixed) {
+      spmm_Yt_bf(h, bf_panel(h, h->Q_bf, h->m, kbp, Q, kbp), kbp, T, kbp);
+      spmm_Y_bf(h, bf_panel(h, h->T_bf, h->n, kbp, T, kbp), kbp, H, kbp);
+    } else {
+      spmm_Yt(h, Q, kbp, kbp, T, kbp);
+      spmm_Y(h, T, kbp, kbp, H, kbp);              // Q = A (A^T Q)
+    }
   }
   orth_block(h, h->m, kbp, H, kbp, Q, kbp);        // eigSVD(Q): its U is an orthonormal basis (Lemma 2)
   h->Kq = kbp;
@@ -490,6 +538,8 @@ void svt_initialise(mc_handle h, const mc_params *prm) {
   const mc_params &P = h->prm;
   MC_REQUIRE(P.delta > 0 && P.eps > 0 && P.l >= 1 && P.s >= 0 && P.i_max >= 1, "invalid SVT parameters");
   MC_REQUIRE(P.recycle >= 0 && P.recycle <= 3, "recycle must be 0..3");
+  MC_REQUIRE(P.precision == 0 || P.precision == 1, "precision must be 0 (float32) or 1 (bf16 panels)");
+  h->precision = P.precision;
   h->tau = P.tau > 0 ? P.tau : 5.0 * std::sqrt((double)h->m * (double)h->n);
   // Y currently holds P_Phi(M) only if no rSVD/SVT changed it; start from M.
   copy_in(h->stream, h->y.p, h->mval.p, sizeof(float) * h->nnz);
@@ -833,6 +883,7 @@ void mc_destroy(mc_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   Alloc &a = h->alloc;
+  for (DBuf *b : {&h->Om_bf, &h->Q_bf, &h->T_bf}) b->release(a);
   for (DBuf *b : {&h->rp, &h->ci, &h->mval, &h->y, &h->rix, &h->cp, &h->ri, &h->perm, &h->yc, &h->Om, &h->Q, &h->H, &h->Tmp,
                   &h->T, &h->Bt, &h->G, &h->C, &h->Rinv, &h->lam, &h->W, &h->Wsel, &h->scale, &h->U, &h->V, &h->Ub,
                   &h->Vb, &h->seg_sq, &h->dsum, &h->tn_part, &h->sp_part, &h->eig_work, &h->flags})
@@ -874,6 +925,12 @@ mc_status mc_rsvd_pi(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t c
                      int *k_out) {
   if (!h) return MC_EINVAL;
   return guarded([&]() { return do_rsvd(h, false, k, s, p, seed, call_id, U, S, V, k_out); });
+}
+
+mc_status mc_set_precision(mc_handle h, int precision) {
+  if (!h || (precision != 0 && precision != 1)) return MC_EINVAL;
+  h->precision = precision;
+  return MC_OK;
 }
 
 mc_status mc_svt_reset(mc_handle h) {

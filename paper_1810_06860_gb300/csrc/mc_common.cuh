@@ -108,6 +108,12 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
 // rows_in: rows of X (sizes the column chunks so the panel slice stays in L2).
 void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, int64_t rows_in,
           const float *X, int ld_x, int K, float *out, int ld_out, float *partial);
+// As spmm with a bf16 panel X (K, ld_x multiples of 8, K <= 256), float32
+// accumulation and output (mixed-precision form).
+void spmm_bf16(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, const void *Xbf, int ld_x,
+               int K, float *out, int ld_out, float *partial);
+// out (rows x ld_out, bf16) = round(in[:, 0:cols]), zero columns after cols.
+void to_bf16(cudaStream_t st, int64_t rows, int cols, const float *in, int ld_in, void *out, int ld_out);
 // y = P_Phi(M) scaled: y[e] = alpha * mval[e]
 void scale_values(cudaStream_t st, int64_t nnz, const float *src, float alpha, float *dst);
 // Yc[p] = Y[perm[p]]
