@@ -43,6 +43,9 @@ M_ROWS, N_COLS, N_PAIRS, HOLDOUT, SEED = 138_000, 27_000, 20_000_000, 0.1, 0
 DELTA = 1.9
 K_BKI, S_OVER, P_BKI = 50, 10, 3
 HBM_FALLBACK_GBS = 6800.0
+# Serving: a bounded sample of the Poisson job stream (m, n log-uniform in
+# [256, 8192], 5-50% observed, rank 5-50), submitted at its arrival times.
+SERVE_JOBS, SERVE_RATE, SERVE_SLOTS, SERVE_IMAX = 48, 16.0, 16, 300
 
 
 def workload_config():
@@ -263,7 +266,9 @@ def run_ours(args, rank, world, local):
     tr = committed_traffic("k_sparse.cu")
     roofline = {"bound": "hbm", "kernel": "spmm (Y X over CSR and Y^T X over CSC)", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "traffic": round(tr["traffic_over_algorithmic"] * sp_bytes / max(sp_launch, 1)) if tr else None,
+                "traffic_source": ("ncu DRAM bytes of the SpMM on a 1.6e7-pair case, scaled to this launch by "
+                                   "algorithmic bytes" if tr else None),
                 "algorithmic_bytes_per_launch": sp_bytes / max(sp_launch, 1),
                 "share_of_step": round(sp_ms / t_ms, 3) if t_ms > 0 else None}
     # ---- mixed-precision form: same workload, bf16 Krylov panels ---------------
@@ -296,6 +301,7 @@ def run_ours(args, rank, world, local):
     bki_mixed_ms = e0.elapsed_time(e1) / nb
     hbm.close()
     del rp, ci, va
+    serving = run_serving(mc, SERVE_JOBS) if not args.no_serving else None
     mixed = {"value": round(args.steps * world / (t_mixed / 1e3), 3), "unit": "iters/s",
              "rsvd_bki_ms": round(bki_mixed_ms, 3), "heldout_rmse": round(rmse_m, 5),
              "heldout_rmse_minus_plain": round(rmse_m - rmse, 6),
@@ -330,7 +336,7 @@ def run_ours(args, rank, world, local):
                            timed_iterations=f"{args.warmup + 1}..{args.warmup + args.steps}",
                            k_last=last["k"], r_last=last["r"], p_last=last["p"], err_last=round(last["err"], 6),
                            heldout_rmse=round(rmse, 5)),
-            "rsvd_bki_ms": round(bki_ms, 3), "rsvd_bki_timing_ms": bki_tm, "mixed_precision": mixed,
+            "rsvd_bki_ms": round(bki_ms, 3), "rsvd_bki_timing_ms": bki_tm, "mixed_precision": mixed, "serving": serving,
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(), "gpu_launches": int(launches),
             "timing_ms": {k: round(v["ms"], 3) for k, v in tm.items()}}
@@ -340,6 +346,88 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def serving_sample(num_jobs: int):
+    """The first num_jobs jobs of the 2,000-job Poisson stream (seed 0)."""
+    spec = mc_synth.serving_jobs(2000, rate=SERVE_RATE, seed=SEED)[:num_jobs]
+    obs = [mc_synth.lowrank_uniform(j["m"], j["n"], j["rank"], nobs=j["nobs"], seed=j["seed"]) for j in spec]
+    return spec, obs
+
+
+def run_serving(mc, num_jobs: int):
+    """Solves/s and p50/p99 latency of the serving form on a sample of the
+    job stream: each job is a whole SVT solve (tau = 5 sqrt(mn), delta =
+    1.2/frac, eps = 1e-4, i_max = SERVE_IMAX), submitted at its arrival time."""
+    spec, obs = serving_sample(num_jobs)
+    prms = [mc.params(tau=5.0 * math.sqrt(o.m * o.n), delta=1.2 / j["frac"], eps=1e-4, i_max=SERVE_IMAX,
+                      seed=j["seed"]) for j, o in zip(spec, obs)]
+    nnz = [int(o.row_ptr[-1]) for o in obs]
+    l0 = mc.load().mc_launch_count()
+    with mc.Server(max_active=SERVE_SLOTS) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for j, o, p in zip(spec, obs, prms):
+            dt = j["arrival"] - spec[0]["arrival"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit_observed(o, p))
+        res = [srv.wait(i, 3600) for i in ids]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = np.array([r["latency_s"] for r in res])
+    held = []
+    for o, r in zip(obs, res):
+        if r.get("Us") is None:
+            continue
+        # relative RMSE on a fixed sample of unobserved entries (true low-rank M)
+        rng = np.random.default_rng(0)
+        ii = rng.integers(0, o.m, 4096)
+        jj = rng.integers(0, o.n, 4096)
+        pred = np.einsum("ij,ij->i", r["Us"][ii].astype(np.float64), r["V"][jj].astype(np.float64))
+        truth = o.dense[ii, jj].astype(np.float64)
+        held.append(float(np.sqrt(np.mean((pred - truth) ** 2)) / np.sqrt(np.mean(truth ** 2))))
+    return {"solves_per_s": round(len(res) / wall, 3), "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+            "p50_queue_s": round(float(np.percentile([r["queue_s"] for r in res], 50)), 4),
+            "jobs": len(res), "converged": int(sum(r["converged"] for r in res)),
+            "iters_total": int(sum(r["iters"] for r in res)), "nnz_total": int(sum(nnz)),
+            "median_rel_rmse_unobserved": round(float(np.median(held)), 5) if held else None,
+            "wall_s": round(wall, 3), "slots": SERVE_SLOTS, "peak_active": st["peak_active"],
+            "peak_in_use_gb": round(st["peak_in_use_bytes"] / 1e9, 3),
+            "gpu_launches": int(mc.load().mc_launch_count() - l0),
+            "workload": f"first {len(res)} jobs of a 2,000-job Poisson stream at {SERVE_RATE} jobs/s: m, n "
+                        f"log-uniform [256, 8192], 5-50% observed, rank 5-50; i_max {SERVE_IMAX}"}
+
+
+def run_case(args):
+    """A small fixed case of one kernel class, for profiler captures: inputs
+    larger than L2 but a few hundred MB on the device, a handful of launches."""
+    import torch
+
+    import paper_1810_06860_gb300 as mc
+
+    mc.load()
+    if args.case in ("spmm", "sddmm"):
+        o = mc_synth.ratings(120_000, 24_000, 16_000_000, seed=3)
+        with mc.Handle.from_observed(o) as h:
+            if args.case == "spmm":
+                for K in (12, 60, 240):
+                    for trans in (False, True):
+                        X = torch.randn((o.m if trans else o.n), K, device="cuda")
+                        h.spmm(X, trans=trans, device=True)
+            else:
+                prm = mc.params(tau=5.0 * math.sqrt(o.m * o.n), delta=DELTA, eps=1e-4, recycle=1, seed=SEED)
+                for _ in range(3):
+                    h.svt_step(prm)
+    elif args.case == "serve":
+        print(json.dumps(run_serving(mc, args.steps)), flush=True)
+    elif args.case == "gram":
+        X = torch.randn(138_000, 240, device="cuda")
+        for _ in range(3):
+            mc.gram(X, tensor_cores=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "status": "ok"}), flush=True)
 
 
 def run_reference(args, rank, world, local):
@@ -377,11 +465,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--case", choices=["spmm", "sddmm", "gram", "serve"], default=None,
+                    help="run one small kernel case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
-    if args.warmup < 1 or args.steps < 1:
-        ap.error("--steps and --warmup must be >= 1")
+    if args.warmup < 3 or args.steps < 1:
+        ap.error("--steps must be >= 1 and --warmup >= 3")
     rank, world, local = dist_init()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)

@@ -193,6 +193,87 @@ mc_status mc_timing_enable(mc_handle h, int on);
 /* out: MC_T_COUNT entries (host).  Synchronises the handle's stream. */
 mc_status mc_timing_read(mc_handle h, mc_timing *out);
 
+/* ---- serving: many completion jobs on one GPU ---------------------------
+ *
+ * A server runs whole SVT solves (Alg. 6 until err < eps or i_max) for jobs
+ * submitted at any time.  Jobs are admitted in arrival order as soon as a
+ * slot is free and the job's device-memory footprint fits the budget
+ * (continuous batching: jobs that arrive while others run join them).  Each
+ * admitted job keeps its sparse iterate Y, recycled subspace and factors
+ * resident on the device and issues its kernels on its own CUDA stream, so
+ * the work of different jobs overlaps on the GPU.  Results do not depend on
+ * what else runs: every kernel is deterministic.  The paper solves one
+ * problem at a time; this form has no counterpart there. */
+typedef struct mc_server_s *mc_server;
+
+typedef struct {
+  int64_t m, n, nnz;          /* job shape; nnz observed entries */
+  const int64_t *row_ptr;     /* host, m+1 entries, CSR of P_Phi(M) */
+  const int32_t *col;         /* host, nnz column indices, sorted within rows */
+  const float *val;           /* host, nnz observed values M_ij */
+  mc_params params;           /* tau, delta, eps, i_max, ... of Alg. 6 */
+} mc_job_desc;
+
+typedef struct {
+  mc_status status;           /* MC_OK (converged), MC_ENOTCONVERGED, MC_ECANCELLED or the failure */
+  int iters, r, converged;
+  double err;                 /* last ||P_Phi(X - M)||_F / ||P_Phi(M)||_F */
+  int64_t m, n;
+  const float *Us;            /* host m x r, U diag(sigma - tau) (row-major); owned by the server */
+  const float *V;             /* host n x r */
+  const float *sigma;         /* host r singular values before shrinking, descending */
+  double queue_s;             /* seconds from mc_submit to admission */
+  double latency_s;           /* seconds from mc_submit to completion */
+  size_t footprint_bytes;     /* admission estimate */
+  size_t device_bytes_peak;   /* device memory the job held at its peak */
+} mc_result;
+
+typedef struct {
+  size_t budget_bytes, in_use_bytes, peak_in_use_bytes;
+  int active, peak_active, queued, slots;
+  int64_t admitted, completed;
+} mc_server_info;
+
+/* mc_server_create: budget_bytes of device memory for admitted jobs' estimated
+ * footprints (0: half of the free memory of the device at creation);
+ * max_active concurrent jobs (1..256), each driven by one host worker thread;
+ * device: CUDA device ordinal.  simulate != 0 runs no GPU work: a job takes
+ * params.i_max microseconds and returns no factors (tests of the scheduling
+ * logic on hosts without a GPU). */
+mc_status mc_server_create(mc_server *out, size_t budget_bytes, int max_active, int device, int simulate);
+
+/* mc_server_destroy: cancels queued and running jobs, waits for the workers
+ * (a running job stops after its current iteration) and frees everything. */
+void mc_server_destroy(mc_server s);
+
+/* mc_submit: copies the job's host arrays and queues it; returns at once with
+ * its id.  MC_EINVAL for bad shapes or pointers; the CSR itself is checked
+ * when the job starts (its result then carries MC_EINVAL).  A job whose
+ * footprint exceeds the whole budget runs alone when nothing else does. */
+mc_status mc_submit(mc_server s, const mc_job_desc *job, uint64_t *job_id);
+
+/* mc_poll: non-blocking.  MC_PENDING while the job is queued or running;
+ * otherwise fills out and returns MC_OK (out->status holds the job's own
+ * outcome) or MC_ECANCELLED.  MC_EINVAL for an unknown id.  The pointers in
+ * out stay valid until mc_result_release or mc_server_destroy. */
+mc_status mc_poll(mc_server s, uint64_t job_id, mc_result *out);
+
+/* mc_wait: blocks until the job has finished or timeout_s has passed
+ * (MC_ETIMEOUT). */
+mc_status mc_wait(mc_server s, uint64_t job_id, double timeout_s);
+
+/* mc_cancel: a queued job is dropped; a running one stops after its current
+ * iteration.  Its result has status MC_ECANCELLED. */
+mc_status mc_cancel(mc_server s, uint64_t job_id);
+
+/* mc_result_release: frees a finished job's result (MC_EBUSY if not finished). */
+mc_status mc_result_release(mc_server s, uint64_t job_id);
+
+/* mc_server_stats: occupancy counters.  mc_server_admit_order writes up to
+ * cap job ids in the order they were admitted and returns how many there are. */
+mc_status mc_server_stats(mc_server s, mc_server_info *out);
+int64_t mc_server_admit_order(mc_server s, uint64_t *ids, int64_t cap);
+
 /* ---- building blocks, exposed for testing and reuse -------------------- */
 
 /* Omega (n x k) of Alg. 1/4/5 step 1 drawn from Philox4x32-10 with counter

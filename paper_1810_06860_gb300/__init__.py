@@ -17,7 +17,7 @@ import numpy as np
 from . import _native
 from ._native import McIterInfo, McParams
 
-__all__ = ["Handle", "McError", "params", "omega", "eig_sym", "gram", "load", "lib_path"]
+__all__ = ["Handle", "Server", "McError", "params", "omega", "eig_sym", "gram", "load", "lib_path"]
 
 load = _native.load
 lib_path = _native.lib_path
@@ -266,8 +266,89 @@ def eig_sym(A, kw: int):
 def gram(X, tensor_cores: bool = False):
     """X^T X of a tall float32 matrix (SIMT, or tcgen05 tensor cores for K <= 256)."""
     lib = load()
-    X = np.ascontiguousarray(X, np.float32)
+    px, keep = _ptr(X, np.float32)
     G = np.empty((X.shape[1], X.shape[1]), np.float32)
     fn = lib.mc_gram_tc if tensor_cores else lib.mc_gram
-    _check(fn(X.shape[0], X.shape[1], X.ctypes.data_as(C.c_void_p), G.ctypes.data_as(C.c_void_p)), fn.__name__)
+    _check(fn(X.shape[0], X.shape[1], px, G.ctypes.data_as(C.c_void_p)), fn.__name__)
     return G
+
+
+class Server:
+    """Serving form: whole SVT solves of many jobs on one GPU (mc_server_*).
+
+    Jobs are admitted in arrival order as slots and the device-memory budget
+    allow; each runs on its own stream, so jobs overlap on the GPU."""
+
+    def __init__(self, budget_bytes: int = 0, max_active: int = 8, device: int = 0, simulate: bool = False):
+        self._lib = load()
+        s = C.c_void_p()
+        _check(self._lib.mc_server_create(C.byref(s), int(budget_bytes), int(max_active), int(device),
+                                          1 if simulate else 0), "mc_server_create")
+        self._s = s
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._lib.mc_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, m: int, n: int, row_ptr, col, val, prm: McParams) -> int:
+        rp = np.ascontiguousarray(row_ptr, np.int64)
+        ci = np.ascontiguousarray(col, np.int32)
+        vv = np.ascontiguousarray(val, np.float32)
+        d = _native.McJobDesc(int(m), int(n), int(len(ci)), rp.ctypes.data, ci.ctypes.data, vv.ctypes.data, prm)
+        jid = C.c_uint64(0)
+        _check(self._lib.mc_submit(self._s, C.byref(d), C.byref(jid)), "mc_submit")
+        return int(jid.value)
+
+    def submit_observed(self, obs, prm: McParams) -> int:
+        return self.submit(obs.m, obs.n, obs.row_ptr, obs.col, obs.val, prm)
+
+    def poll(self, job_id: int, factors: bool = True):
+        """None while the job is queued or running, else its result (a dict)."""
+        res = _native.McResult()
+        st = self._lib.mc_poll(self._s, C.c_uint64(job_id), C.byref(res))
+        if st == _native.MC_PENDING:
+            return None
+        if st not in (_native.MC_OK, _native.MC_ECANCELLED):
+            _check(st, "mc_poll")
+        out = {f: getattr(res, f) for f, _ in _native.McResult._fields_ if f not in ("Us", "V", "sigma")}
+        r = res.r
+        if factors and r > 0 and res.Us:
+            out["Us"] = np.ctypeslib.as_array(res.Us, shape=(res.m, r)).copy()
+            out["V"] = np.ctypeslib.as_array(res.V, shape=(res.n, r)).copy()
+            out["sigma"] = np.ctypeslib.as_array(res.sigma, shape=(r,)).copy()
+        return out
+
+    def wait(self, job_id: int, timeout_s: float = 3600.0):
+        st = self._lib.mc_wait(self._s, C.c_uint64(job_id), float(timeout_s))
+        _check(st, "mc_wait")
+        return self.poll(job_id)
+
+    def cancel(self, job_id: int):
+        _check(self._lib.mc_cancel(self._s, C.c_uint64(job_id)), "mc_cancel")
+
+    def release(self, job_id: int):
+        _check(self._lib.mc_result_release(self._s, C.c_uint64(job_id)), "mc_result_release")
+
+    def stats(self) -> dict:
+        info = _native.McServerInfo()
+        _check(self._lib.mc_server_stats(self._s, C.byref(info)), "mc_server_stats")
+        return {f: getattr(info, f) for f, _ in _native.McServerInfo._fields_}
+
+    def admit_order(self):
+        n = self._lib.mc_server_admit_order(self._s, None, 0)
+        buf = (C.c_uint64 * max(n, 1))()
+        n = self._lib.mc_server_admit_order(self._s, buf, n)
+        return [int(buf[i]) for i in range(n)]

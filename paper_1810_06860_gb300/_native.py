@@ -37,6 +37,24 @@ class McAllocator(C.Structure):
     _fields_ = [("ctx", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
 
 
+class McJobDesc(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("params", McParams)]
+
+
+class McResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("r", C.c_int), ("converged", C.c_int),
+                ("err", C.c_double), ("m", C.c_int64), ("n", C.c_int64), ("Us", C.POINTER(C.c_float)),
+                ("V", C.POINTER(C.c_float)), ("sigma", C.POINTER(C.c_float)), ("queue_s", C.c_double),
+                ("latency_s", C.c_double), ("footprint_bytes", C.c_size_t), ("device_bytes_peak", C.c_size_t)]
+
+
+class McServerInfo(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("in_use_bytes", C.c_size_t), ("peak_in_use_bytes", C.c_size_t),
+                ("active", C.c_int), ("peak_active", C.c_int), ("queued", C.c_int), ("slots", C.c_int),
+                ("admitted", C.c_int64), ("completed", C.c_int64)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "mc_params_default": (None, [C.POINTER(McParams)]),
@@ -63,6 +81,15 @@ _SIGS = {
     "mc_gram": (C.c_int, [C.c_int64, C.c_int, _P, _P]),
     "mc_gram_tc": (C.c_int, [C.c_int64, C.c_int, _P, _P]),
     "mc_gram_noalloc": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int, _P, C.c_int, _P]),
+    "mc_server_create": (C.c_int, [C.POINTER(_P), C.c_size_t, C.c_int, C.c_int, C.c_int]),
+    "mc_server_destroy": (None, [_P]),
+    "mc_submit": (C.c_int, [_P, C.POINTER(McJobDesc), C.POINTER(C.c_uint64)]),
+    "mc_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(McResult)]),
+    "mc_wait": (C.c_int, [_P, C.c_uint64, C.c_double]),
+    "mc_cancel": (C.c_int, [_P, C.c_uint64]),
+    "mc_result_release": (C.c_int, [_P, C.c_uint64]),
+    "mc_server_stats": (C.c_int, [_P, C.POINTER(McServerInfo)]),
+    "mc_server_admit_order": (C.c_int64, [_P, C.POINTER(C.c_uint64), C.c_int64]),
 }
 
 _lib = None

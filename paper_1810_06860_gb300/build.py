@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libmc.so")
-SOURCES = ["k_rng.cu", "k_sparse.cu", "k_dense.cu", "k_eig.cu", "k_tc.cu", "mc_api.cu"]
+SOURCES = ["k_rng.cu", "k_sparse.cu", "k_dense.cu", "k_eig.cu", "k_tc.cu", "mc_api.cu", "mc_serve.cu"]
 HEADERS = [os.path.join(CSRC, "mc_common.cuh"), os.path.join(ROOT, "include", "mc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
