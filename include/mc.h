@@ -226,6 +226,7 @@ typedef struct {
   double latency_s;           /* seconds from mc_submit to completion */
   size_t footprint_bytes;     /* admission estimate */
   size_t device_bytes_peak;   /* device memory the job held at its peak */
+  const char *message;        /* failure message ("" on success); owned by the server */
 } mc_result;
 
 typedef struct {

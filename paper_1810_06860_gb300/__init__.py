@@ -323,7 +323,8 @@ class Server:
             return None
         if st not in (_native.MC_OK, _native.MC_ECANCELLED):
             _check(st, "mc_poll")
-        out = {f: getattr(res, f) for f, _ in _native.McResult._fields_ if f not in ("Us", "V", "sigma")}
+        out = {f: getattr(res, f) for f, _ in _native.McResult._fields_ if f not in ("Us", "V", "sigma", "message")}
+        out["message"] = (res.message or b"").decode(errors="replace")
         r = res.r
         if factors and r > 0 and res.Us:
             out["Us"] = np.ctypeslib.as_array(res.Us, shape=(res.m, r)).copy()

@@ -46,7 +46,8 @@ class McResult(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("r", C.c_int), ("converged", C.c_int),
                 ("err", C.c_double), ("m", C.c_int64), ("n", C.c_int64), ("Us", C.POINTER(C.c_float)),
                 ("V", C.POINTER(C.c_float)), ("sigma", C.POINTER(C.c_float)), ("queue_s", C.c_double),
-                ("latency_s", C.c_double), ("footprint_bytes", C.c_size_t), ("device_bytes_peak", C.c_size_t)]
+                ("latency_s", C.c_double), ("footprint_bytes", C.c_size_t), ("device_bytes_peak", C.c_size_t),
+                ("message", C.c_char_p)]
 
 
 class McServerInfo(C.Structure):

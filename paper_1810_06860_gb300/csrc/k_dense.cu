@@ -68,11 +68,115 @@ gemm_tn_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x,
   }
 }
 
+// ---- asynchronous global -> shared copies (cp.async, 16 bytes) -------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---- gemm_tn for narrow panels (K1, K2 <= 64): one T x T output tile --------
+// T in {16, 32, 64}.  The block's 256 threads form 256 / (T/4)^2 groups; a
+// thread owns a 4 x 4 piece of the tile and its group walks every G-th row of
+// the staged chunk.  Chunks of CH rows of X (and Y) stream through STAGES
+// shared-memory buffers with cp.async, so loads of later chunks are in flight
+// while a chunk is multiplied.  For the symmetric Gram the pieces below the
+// diagonal are skipped (the reducer mirrors them).  The groups' sums are added
+// in group order, and each block writes one partial tile.
+constexpr int TNS_STAGES = 3;
+template <int T>
+struct TnSmall {
+  static constexpr int TQ = T / 4, GT = TQ * TQ, G = 256 / GT, CH = (T == 64) ? 64 : 128;
+  static constexpr size_t smem_bytes(bool same) { return sizeof(float) * TNS_STAGES * CH * T * (same ? 1 : 2); }
+};
+
+template <int T>
+__global__ void __launch_bounds__(256)
+gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ Y,
+                     int ld_y, int64_t rows_per_split, int sym, int same, float *__restrict__ partial) {
+  using P = TnSmall<T>;
+  extern __shared__ __align__(16) float tns[];
+  float *xs = tns;                                          // [STAGES][CH][T]
+  float *ys = same ? tns : tns + TNS_STAGES * P::CH * T;    // [STAGES][CH][T]
+  const int tid = threadIdx.x;
+  const int g = tid / P::GT, q = tid % P::GT, ty = q / P::TQ, tx = q % P::TQ;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_split;
+  const int64_t r1 = min(R, r0 + rows_per_split);
+  const int nchunks = r1 > r0 ? static_cast<int>((r1 - r0 + P::CH - 1) / P::CH) : 0;
+  auto issue = [&](int c) {
+    const int stg = c % TNS_STAGES;
+    const int64_t rb = r0 + (int64_t)c * P::CH;
+    for (int e = tid; e < P::CH * P::TQ; e += 256) {
+      const int rr = e / P::TQ, c4 = (e % P::TQ) * 4;
+      const int64_t r = rb + rr;
+      const bool okx = r < r1 && c4 < K1;
+      cp_async16(xs + ((size_t)stg * P::CH + rr) * T + c4, okx ? X + r * ld_x + c4 : X, okx ? 16 : 0);
+      if (!same) {
+        const bool oky = r < r1 && c4 < K2;
+        cp_async16(ys + ((size_t)stg * P::CH + rr) * T + c4, oky ? Y + r * ld_y + c4 : Y, oky ? 16 : 0);
+      }
+    }
+  };
+#pragma unroll
+  for (int c = 0; c < TNS_STAGES - 1; ++c) {
+    if (c < nchunks) issue(c);
+    cp_async_commit();
+  }
+  const bool active = ty * 4 < K1 && tx * 4 < K2 && !(sym && ty > tx);
+  float acc[4][4] = {};
+  for (int c = 0; c < nchunks; ++c) {
+    if (c + TNS_STAGES - 1 < nchunks) issue(c + TNS_STAGES - 1);
+    cp_async_commit();
+    cp_async_wait<TNS_STAGES - 1>();
+    __syncthreads();
+    const int stg = c % TNS_STAGES;
+    const float *xb = xs + (size_t)stg * P::CH * T, *yb = ys + (size_t)stg * P::CH * T;
+    if (active) {
+#pragma unroll 4
+      for (int rr = g; rr < P::CH; rr += P::G) {
+        const float4 a = *reinterpret_cast<const float4 *>(xb + rr * T + ty * 4);
+        const float4 b = *reinterpret_cast<const float4 *>(yb + rr * T + tx * 4);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  float *dst = partial + (int64_t)blockIdx.x * T * T;
+  if (P::G == 1) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      *reinterpret_cast<float4 *>(dst + (ty * 4 + u) * T + tx * 4) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+    return;
+  }
+  float *red = tns;  // [G][T][T], fits in the stage buffers
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    *reinterpret_cast<float4 *>(red + ((size_t)g * T + ty * 4 + u) * T + tx * 4) =
+        make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+  __syncthreads();
+  for (int e = tid; e < T * T; e += 256) {
+    float v = 0.f;
+#pragma unroll
+    for (int gg = 0; gg < P::G; ++gg) v += red[(size_t)gg * T * T + e];
+    dst[e] = v;
+  }
+}
+
 // Sum of the per-split partial tiles, in split order: a block covers 32
 // outputs with 8 lanes of split groups each, then adds the 8 group sums in order.
 __global__ void __launch_bounds__(256)
 gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ partial, int K1p, int K2p, bool sym,
-                      float *__restrict__ C, int ld_c) {
+                      int mirror, float *__restrict__ C, int ld_c) {
   __shared__ float sh[8][33];
   const int64_t total = (int64_t)K1 * K2;
   const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
@@ -85,7 +189,7 @@ gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ part
       i = static_cast<int>(t / K2);
       j = static_cast<int>(t % K2);
       int si = i, sj = j;
-      if (sym && (j / TN_T) < (i / TN_T)) {  // tile below the diagonal: read the mirrored tile
+      if (sym && (j / mirror) < (i / mirror)) {  // piece below the diagonal: read the mirrored one
         si = j;
         sj = i;
       }
@@ -102,6 +206,108 @@ gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ part
     }
     __syncthreads();
   }
+}
+
+// ---- gemm_nn for narrow panels (K1, K2 <= 64) -------------------------------
+// W (zero-padded to 64 x 64) stays in shared memory; 64-row chunks of X
+// stream through three cp.async buffers.  Thread (ty, tx) computes rows
+// 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 of the chunk's output.
+constexpr int NNS_BM = 64, NNS_STAGES = 3;
+constexpr size_t kNnSmallSmem = sizeof(float) * (64 * 64 + NNS_STAGES * NNS_BM * 64);
+
+__global__ void __launch_bounds__(256)
+gemm_nn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ W,
+                     int ld_w, const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z,
+                     int ld_z, int64_t chunks_per_block) {
+  extern __shared__ __align__(16) float nns[];
+  float *ws = nns;            // [64][64]
+  float *xs = nns + 64 * 64;  // [STAGES][BM][64]
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int64_t nch_total = (R + NNS_BM - 1) / NNS_BM;
+  const int64_t c0 = (int64_t)blockIdx.x * chunks_per_block;
+  const int64_t c1 = min(nch_total, c0 + chunks_per_block);
+  const int nch = c1 > c0 ? static_cast<int>(c1 - c0) : 0;
+  const int K4 = (K1 + 3) / 4;
+  auto issue = [&](int c) {
+    const int stg = c % NNS_STAGES;
+    const int64_t rb = (c0 + c) * NNS_BM;
+    for (int e = tid; e < NNS_BM * 16; e += 256) {
+      const int rr = e / 16, k4 = (e % 16) * 4;
+      const int64_t r = rb + rr;
+      const bool ok = r < R && k4 < K1;
+      cp_async16(xs + ((size_t)stg * NNS_BM + rr) * 64 + k4, ok ? X + r * ld_x + k4 : X, ok ? 16 : 0);
+    }
+  };
+#pragma unroll
+  for (int c = 0; c < NNS_STAGES - 1; ++c) {
+    if (c < nch) issue(c);
+    cp_async_commit();
+  }
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int k = e / 64, j = e % 64;
+    ws[e] = (k < K1 && j < K2) ? W[(int64_t)k * ld_w + j] : 0.f;
+  }
+  float sc[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = tx * 4 + v;
+    sc[v] = j < K2 ? alpha * (colscale ? colscale[j] : 1.0f) : 0.f;
+  }
+  const bool vec_out = (ld_z % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0) && tx * 4 + 3 < K2;
+  for (int c = 0; c < nch; ++c) {
+    if (c + NNS_STAGES - 1 < nch) issue(c + NNS_STAGES - 1);
+    cp_async_commit();
+    cp_async_wait<NNS_STAGES - 1>();
+    __syncthreads();
+    const float *xb = xs + (size_t)(c % NNS_STAGES) * NNS_BM * 64;
+    float acc[4][4] = {};
+    if (tx * 4 < K2) {
+      for (int k4 = 0; k4 < K4; ++k4) {
+        float4 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = *reinterpret_cast<const float4 *>(xb + (ty * 4 + u) * 64 + k4 * 4);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) b[t] = *reinterpret_cast<const float4 *>(ws + (k4 * 4 + t) * 64 + tx * 4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float av[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            acc[u][0] = fmaf(av[t], b[t].x, acc[u][0]);
+            acc[u][1] = fmaf(av[t], b[t].y, acc[u][1]);
+            acc[u][2] = fmaf(av[t], b[t].z, acc[u][2]);
+            acc[u][3] = fmaf(av[t], b[t].w, acc[u][3]);
+          }
+        }
+      }
+      const int64_t rb = (c0 + c) * NNS_BM;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t r = rb + ty * 4 + u;
+        if (r >= R) continue;
+        float *z = Z + r * ld_z + tx * 4;
+        if (vec_out) {
+          float4 o = make_float4(acc[u][0] * sc[0], acc[u][1] * sc[1], acc[u][2] * sc[2], acc[u][3] * sc[3]);
+          if (beta != 0.f) {
+            const float4 p = *reinterpret_cast<const float4 *>(z);
+            o.x += beta * p.x;
+            o.y += beta * p.y;
+            o.z += beta * p.z;
+            o.w += beta * p.w;
+          }
+          *reinterpret_cast<float4 *>(z) = o;
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            if (tx * 4 + v >= K2) continue;
+            z[v] = (beta != 0.f ? beta * z[v] : 0.f) + acc[u][v] * sc[v];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
 }
 
 // ============================================================ gemm_nn ======
@@ -173,82 +379,78 @@ gemm_nn_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x,
   }
 }
 
-// ===================================================== chol_inv (one warp) ==
-// K <= 64: the same factorisation and inverse by a single warp (no block
-// barriers).  Lane l owns rows l and l + 32 of the working matrices.
-__global__ void __launch_bounds__(32)
-chol_inv_warp_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
-                     float ref_tol, float *__restrict__ Rinv) {
-  __shared__ float L[64][65];
-  __shared__ float X[64][65];
-  __shared__ float keepf[64];
-  const int lane = threadIdx.x;
-  float tr = 0.f, mx = 0.f;
-  for (int i = lane; i < K; i += 32) {
-    const float gi = G[(int64_t)i * ld + i];
-    tr += gi;
-    mx = fmaxf(mx, gi);
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    tr += __shfl_xor_sync(0xffffffffu, tr, off);
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  }
-  const float shift = shift_rel * tr / K;
-  const float drop = fmaxf(1e-30f, 1e-12f * mx) + shift;
-  for (int i = lane; i < K; i += 32)
-    keepf[i] = (ref_diag && !(G[(int64_t)i * ld + i] > ref_tol * ref_diag[i])) ? 0.f : 1.f;
-  __syncwarp();
-  for (int i = 0; i < K; ++i)
-    for (int j = lane; j < K; j += 32) {
-      const bool live = keepf[i] != 0.f && keepf[j] != 0.f;
-      L[i][j] = (j <= i && live) ? G[(int64_t)i * ld + j] + (i == j ? shift : 0.f) : 0.f;
+// ============================================== chol_inv (narrow blocks) ==
+// K <= 128: G + shift I = L L^T and L^{-1} together, right-looking, in shared
+// memory.  Step j scales column j of L by 1/sqrt(pivot) and row j of the
+// running right-hand side B (B = I at the start; row j of B becomes row j of
+// L^{-1}); then every row a > j is updated by one warp over its entries:
+// columns b <= j of B (B[a][b] -= L[a][j] X[j][b]) and columns j < b <= a of
+// L (the trailing update).  Two barriers per step, K steps.  The diagonal of
+// L is never overwritten (its final value is kept in dg), so the pivot of the
+// next step can be read right after the second barrier.
+__global__ void __launch_bounds__(1024)
+chol_inv_small_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
+                      float ref_tol, float *__restrict__ Rinv) {
+  extern __shared__ float sh[];
+  const int ls = (K % 2 == 0) ? K + 1 : K;  // odd row stride: column reads are conflict-free
+  float *L = sh;                            // K x ls
+  float *B = L + (size_t)K * ls;            // K x ls
+  float *flags = B + (size_t)K * ls;        // K
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int wid = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  __shared__ float s_tr, s_max;
+  if (tid < 32) {
+    float tr = 0.f, mx = 0.f;
+    for (int i = lane; i < K; i += 32) {
+      const float gi = G[(int64_t)i * ld + i];
+      tr += gi;
+      mx = fmaxf(mx, gi);
     }
-  __syncwarp();
+    for (int off = 16; off > 0; off >>= 1) {
+      tr += __shfl_xor_sync(0xffffffffu, tr, off);
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if (lane == 0) {
+      s_tr = tr;
+      s_max = mx;
+    }
+  }
+  for (int i = tid; i < K; i += nt)
+    flags[i] = (ref_diag && !(G[(int64_t)i * ld + i] > ref_tol * ref_diag[i])) ? 0.f : 1.f;
+  __syncthreads();
+  const float shift = shift_rel * s_tr / K;
+  const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
+  for (int t = tid; t < K * K; t += nt) {
+    const int i = t / K, j = t % K;
+    const bool live = flags[i] != 0.f && flags[j] != 0.f;
+    L[i * ls + j] = (j <= i && live) ? G[(int64_t)i * ld + j] + (i == j ? shift : 0.f) : 0.f;
+    B[i * ls + j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
   for (int j = 0; j < K; ++j) {
-    const float d = L[j][j];
+    const float d = L[j * ls + j];
     const bool keep = d > drop;
     const float inv = keep ? rsqrtf(d) : 0.f;
-    __syncwarp();
-    for (int i = j + 1 + lane; i < K; i += 32) L[i][j] *= inv;
-    if (lane == 0) {
-      L[j][j] = keep ? d * inv : 1.0f;
-      if (!keep) keepf[j] = 0.f;
-    }
-    __syncwarp();
+    // column j of L and row j of L^{-1}
+    for (int i = j + 1 + tid; i < K; i += nt) L[i * ls + j] *= inv;
+    for (int c = tid; c <= j; c += nt) B[j * ls + c] *= inv;
+    if (tid == 0 && !keep) flags[j] = 0.f;
+    __syncthreads();
     if (keep) {
-      // trailing update, the lanes spread over the rows' entries
-      for (int a = j + 1; a < K; ++a) {
-        const float la = L[a][j];
-        for (int b = j + 1 + lane; b <= a; b += 32) L[a][b] -= la * L[b][j];
-      }
-      __syncwarp();
-    }
-  }
-  // forward substitution, lane l solves columns l and l + 32; four partial
-  // sums shorten the dependency chain
-  for (int c = lane; c < K; c += 32) {
-    const bool kc = keepf[c] != 0.f;
-    for (int i = 0; i < K; ++i) {
-      float x = 0.f;
-      if (kc && i >= c && keepf[i] != 0.f) {
-        float a0 = (i == c) ? 1.0f : 0.0f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int l = c;
-        for (; l + 3 < i; l += 4) {
-          a0 -= L[i][l] * X[l][c];
-          a1 -= L[i][l + 1] * X[l + 1][c];
-          a2 -= L[i][l + 2] * X[l + 2][c];
-          a3 -= L[i][l + 3] * X[l + 3][c];
+      for (int a = j + 1 + wid; a < K; a += nw) {
+        const float la = L[a * ls + j];
+        for (int b = lane; b <= a; b += 32) {
+          if (b <= j) B[a * ls + b] -= la * B[j * ls + b];
+          else L[a * ls + b] -= la * L[b * ls + j];
         }
-        for (; l < i; ++l) a0 -= L[i][l] * X[l][c];
-        x = ((a0 + a1) + (a2 + a3)) / L[i][i];
       }
-      X[i][c] = x;
     }
+    __syncthreads();
   }
-  __syncwarp();
-  for (int t = lane; t < K * K; t += 32) {
-    const int i = t / K, j = t % K;
-    Rinv[t] = X[j][i];
+  // R^{-1} = (L^{-1})^T; rows and columns of dropped pivots are zero
+  for (int t = tid; t < K * K; t += nt) {
+    const int i = t / K, c = t % K;
+    Rinv[t] = (flags[i] != 0.f && flags[c] != 0.f && c >= i) ? B[c * ls + i] : 0.f;
   }
 }
 
@@ -355,8 +557,47 @@ chol_inv_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, con
 }
 
 // Column sums of squares of X (R x K): per-chunk partials, then an ordered sum.
-__global__ void colsumsq_partial_kernel(int64_t R, int K, const float *__restrict__ X, int ld, int64_t rows_per,
-                                        float *__restrict__ part) {
+// A block's 256 threads cover K4 = ceil(K/4) float4 columns and 256 / K4 row
+// lanes (K4 <= 64); lane sums are added in lane order in shared memory.
+__global__ void __launch_bounds__(256)
+colsumsq_partial_kernel(int64_t R, int K, const float *__restrict__ X, int ld, int64_t rows_per,
+                        float *__restrict__ part) {
+  __shared__ float4 sh[256];
+  const int K4 = (K + 3) / 4;
+  const int lanes = 256 / K4;
+  const int tid = threadIdx.x, c4 = tid % K4, rl = tid / K4;
+  const int64_t r0 = blockIdx.x * rows_per, r1 = min(R, r0 + rows_per);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (rl < lanes) {
+#pragma unroll 4
+    for (int64_t r = r0 + rl; r < r1; r += lanes) {
+      const float4 v = *reinterpret_cast<const float4 *>(X + r * ld + c4 * 4);
+      acc.x = fmaf(v.x, v.x, acc.x);
+      acc.y = fmaf(v.y, v.y, acc.y);
+      acc.z = fmaf(v.z, v.z, acc.z);
+      acc.w = fmaf(v.w, v.w, acc.w);
+    }
+  }
+  sh[tid] = acc;
+  __syncthreads();
+  if (tid < K4) {
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int l = 0; l < lanes; ++l) {
+      const float4 u = sh[l * K4 + tid];
+      t.x += u.x;
+      t.y += u.y;
+      t.z += u.z;
+      t.w += u.w;
+    }
+    const float tv[4] = {t.x, t.y, t.z, t.w};
+    for (int q = 0; q < 4; ++q)
+      if (tid * 4 + q < K) part[(int64_t)blockIdx.x * K + tid * 4 + q] = tv[q];
+  }
+}
+
+// Columns beyond 256 (or unaligned panels): one thread per column.
+__global__ void colsumsq_partial_wide_kernel(int64_t R, int K, const float *__restrict__ X, int ld, int64_t rows_per,
+                                             float *__restrict__ part) {
   const int64_t r0 = blockIdx.x * rows_per, r1 = min(R, r0 + rows_per);
   for (int c = threadIdx.x; c < K; c += blockDim.x) {
     float acc = 0.f;
@@ -402,7 +643,10 @@ void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *
   if (K <= 0) return;
   const int nchunk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(608, (R + 63) / 64)));
   const int64_t rows_per = (R + nchunk - 1) / nchunk;
-  colsumsq_partial_kernel<<<nchunk, 128, 0, st>>>(R, K, X, ld, rows_per, scratch);
+  if (K <= 256 && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0)
+    colsumsq_partial_kernel<<<nchunk, 256, 0, st>>>(R, K, X, ld, rows_per, scratch);
+  else
+    colsumsq_partial_wide_kernel<<<nchunk, 128, 0, st>>>(R, K, X, ld, rows_per, scratch);
   MC_CHECK_LAUNCH();
   colsumsq_reduce_kernel<<<K, 256, 0, st>>>(K, nchunk, scratch, out);
   MC_CHECK_LAUNCH();
@@ -422,16 +666,57 @@ static int tn_splits(int64_t R, int tiles) {
   return static_cast<int>(std::min<int64_t>(std::min<int64_t>(want, max_by_rows), 1024));
 }
 
+// narrow panels: tile edge of the small kernel (0: use the tiled kernel)
+static int tn_small_tile(int K1, int K2) {
+  const int k = std::max(K1, K2);
+  return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 64 ? 64 : 0));
+}
+static int tn_small_splits(int64_t R) {
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(304, (R + 63) / 64)));
+}
+
 size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2) {
+  const int T = tn_small_tile(K1, K2);
+  if (T) return (size_t)tn_small_splits(R) * T * T;
   const int K1p = (int)round_up(std::max(K1, 1), TN_T), K2p = (int)round_up(std::max(K2, 1), TN_T);
   const int tiles = (K1p / TN_T) * (K2p / TN_T);
   return (size_t)tn_splits(R, tiles) * K1p * K2p;
+}
+
+template <int T>
+static void launch_tn_small(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y,
+                            int ld_y, bool sym, float *partial, int nsplit, int64_t rps) {
+  const bool same = (X == Y && ld_x == ld_y && K1 == K2);
+  const size_t smem = TnSmall<T>::smem_bytes(same);
+  // the attribute is per kernel and process-wide: always set the largest size
+  // any call needs, so concurrent callers on other threads never lower it
+  MC_CUDA(cudaFuncSetAttribute(gemm_tn_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)TnSmall<T>::smem_bytes(false)));
+  gemm_tn_small_kernel<T><<<nsplit, 256, smem, st>>>(R, K1, K2, X, ld_x, Y, ld_y, rps, (sym && same) ? 1 : 0,
+                                                     same ? 1 : 0, partial);
+  MC_CHECK_LAUNCH();
 }
 
 void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y, int ld_y, float *C,
              int ld_c, bool sym, float *partial) {
   if (K1 <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0 && ld_y % 4 == 0, "gemm_tn: leading dims must be multiples of 4");
+  const int T = tn_small_tile(K1, K2);
+  if (T) {
+    MC_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0,
+               "gemm_tn: panels must be 16-byte aligned");
+    const int nsplit = tn_small_splits(R);
+    const int64_t rps = round_up((R + nsplit - 1) / nsplit, 64);
+    const int ns = static_cast<int>((R + rps - 1) / rps);
+    if (T == 16) launch_tn_small<16>(st, R, K1, K2, X, ld_x, Y, ld_y, sym, partial, ns, rps);
+    else if (T == 32) launch_tn_small<32>(st, R, K1, K2, X, ld_x, Y, ld_y, sym, partial, ns, rps);
+    else launch_tn_small<64>(st, R, K1, K2, X, ld_x, Y, ld_y, sym, partial, ns, rps);
+    const int64_t total = (int64_t)K1 * K2;
+    const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
+    gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, ns, partial, T, T, sym && X == Y, 4, C, ld_c);
+    MC_CHECK_LAUNCH();
+    return;
+  }
   const int K1p = (int)round_up(K1, TN_T), K2p = (int)round_up(K2, TN_T);
   const int ti = K1p / TN_T, tj = K2p / TN_T;
   const int nsplit = tn_splits(R, ti * tj);
@@ -441,7 +726,7 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
   MC_CHECK_LAUNCH();
   const int64_t total = (int64_t)K1 * K2;
   const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
-  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, nsplit, partial, K1p, K2p, sym, C, ld_c);
+  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, nsplit, partial, K1p, K2p, sym, TN_T, C, ld_c);
   MC_CHECK_LAUNCH();
 }
 
@@ -449,6 +734,16 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
              const float *colscale, float alpha, float beta, float *Z, int ld_z) {
   if (R <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0, "gemm_nn: ld_x must be a multiple of 4");
+  if (K1 <= 64 && K2 <= 64 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+    const int64_t nch = (R + NNS_BM - 1) / NNS_BM;
+    const int64_t per = std::max<int64_t>(1, (nch + 152 * 3 - 1) / (152 * 3));
+    const unsigned nb = static_cast<unsigned>((nch + per - 1) / per);
+    MC_CUDA(cudaFuncSetAttribute(gemm_nn_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNnSmallSmem));
+    gemm_nn_small_kernel<<<nb, 256, kNnSmallSmem, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, Z, ld_z,
+                                                        per);
+    MC_CHECK_LAUNCH();
+    return;
+  }
   dim3 grid(static_cast<unsigned>((R + NN_BM - 1) / NN_BM), static_cast<unsigned>((K2 + NN_BN - 1) / NN_BN));
   gemm_nn_kernel<<<grid, 256, 0, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, Z, ld_z);
   MC_CHECK_LAUNCH();
@@ -457,8 +752,13 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag, float ref_tol,
               float *Rinv) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
-  if (K <= 64) {
-    chol_inv_warp_kernel<<<1, 32, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv);
+  if (K <= 128) {
+    const int ls = (K % 2 == 0) ? K + 1 : K;
+    const size_t need = sizeof(float) * (2 * (size_t)K * ls + K);
+    constexpr size_t kMax = sizeof(float) * (2 * 128 * 129 + 128);  // K = 128; fixed for concurrent callers
+    MC_CUDA(cudaFuncSetAttribute(chol_inv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax));
+    const int threads = K <= 32 ? 256 : (K <= 64 ? 512 : 1024);
+    chol_inv_small_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv);
     MC_CHECK_LAUNCH();
     return;
   }
@@ -539,7 +839,7 @@ extern "C" mc_status mc_gram_noalloc(int64_t R, int K, const float *X, int ld, f
     MC_CHECK_LAUNCH();
     const int64_t total = (int64_t)K * K;
     const int nb = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 8));
-    gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K, K, nsplit, scratch, Kp, Kp, true, G, ldg);
+    gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K, K, nsplit, scratch, Kp, Kp, true, TN_T, G, ldg);
     MC_CHECK_LAUNCH();
     return MC_OK;
   } catch (const Err &e) {

@@ -13,6 +13,8 @@
 // atomics touch floating-point data.
 #include "mc_common.cuh"
 
+#include <vector>
+
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -116,15 +118,18 @@ __global__ void csc_scatter_kernel(int64_t m, int64_t n, int nblk, const int *__
 }
 
 // --------------------------------------------------------------- products ---
-template <int G>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// G lane groups per warp (a group owns one gathered panel row at a time), U
+// gathers in flight per group.  Group g takes the segment's entries g, g + G,
+// g + 2G, ... in that order whatever U and the block size are, so those two
+// launch parameters (tuned at run time) never change the result's bits.
+template <int G, int U>
+__global__ void __launch_bounds__(256)
 spmm_seg_kernel(int64_t nseg, const int4 *__restrict__ segs, const int *__restrict__ idx,
                 const float *__restrict__ val, const float *__restrict__ X, int ld_x, int K4,
                 float *__restrict__ out, int ld_out, float *__restrict__ partial) {
-  constexpr int L = 32 / G;  // lanes per group; a group owns one gathered row at a time
-  constexpr int U = G >= 8 ? 1 : (G >= 2 ? 2 : 4);  // gathers in flight per group
+  constexpr int L = 32 / G;  // lanes per group
   const int lane = threadIdx.x & 31;
-  const int64_t seg = blockIdx.x * (int64_t)kWarpsPerBlock + (threadIdx.x >> 5);
+  const int64_t seg = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (seg >= nseg) return;
   const int g = lane / L, li = lane % L;
   const int4 sd = segs[seg];  // (row, begin, end, partial slot or -1)
@@ -458,28 +463,65 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
   MC_CUDA(cudaStreamSynchronize(st));
 }
 
+namespace {
+// default gathers in flight for a lane-group count
+int default_u(int G) { return G >= 8 ? 1 : (G >= 2 ? 2 : 4); }
+int lane_groups(int K4) { return K4 <= 2 ? 16 : (K4 <= 4 ? 8 : (K4 <= 8 ? 4 : (K4 <= 16 ? 2 : 1))); }
+int default_chunk(int64_t rows_in) {
+  // column chunks of at most 128, narrower when the panel slice would not stay
+  // resident in L2 next to the streamed indices (each chunk re-reads them)
+  int chunk = 128;
+  while (chunk > 32 && (double)rows_in * chunk * 4.0 > 40e6) chunk /= 2;
+  return chunk;
+}
+
+template <int G>
+void launch_seg(int u, int64_t blocks, int threads, cudaStream_t st, int64_t nseg, const int4 *segs, const int *idx,
+                const float *val, const float *X, int ld_x, int K4, float *out, int ld_out, float *partial) {
+#define MC_SPMM_ARGS nseg, segs, idx, val, X, ld_x, K4, out, ld_out, partial
+  if (u >= 4 && G * 4 <= 32) spmm_seg_kernel<G, (G * 4 <= 32 ? 4 : 1)><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+  else if (u >= 2 && G * 2 <= 32) spmm_seg_kernel<G, (G * 2 <= 32 ? 2 : 1)><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+  else spmm_seg_kernel<G, 1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+#undef MC_SPMM_ARGS
+}
+}  // namespace
+
+std::vector<SpmmCfg> spmm_candidates(int K, int64_t rows_in) {
+  const int G = lane_groups(std::min(K, 128) / 4);
+  const int dc = default_chunk(rows_in);
+  std::vector<SpmmCfg> c;
+  for (int u : {1, 2, 4}) {
+    if (G * u > 32) continue;
+    for (int threads : {128, 256}) c.push_back({u, threads, dc});
+  }
+  if (K > 32) {
+    const int alt = dc >= 64 ? dc / 2 : dc * 2;
+    c.push_back({default_u(G), 256, alt});
+  }
+  return c;
+}
+
 void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, int64_t rows_in, const float *X,
-          int ld_x, int K, float *out, int ld_out, float *partial) {
+          int ld_x, int K, float *out, int ld_out, float *partial, const SpmmCfg &cfg) {
   if (plan.nseg == 0 || K <= 0) return;
   MC_REQUIRE(K % 4 == 0 && ld_x % 4 == 0 && ld_out % 4 == 0, "spmm: K and leading dims must be multiples of 4");
   MC_REQUIRE(K <= 1024, "spmm: panel width above 1024");
-  // Column chunks of at most 128, narrower when the panel slice would not stay
-  // resident in L2 next to the streamed indices (each chunk re-reads them).
-  int chunk = 128;
-  while (chunk > 32 && (double)rows_in * chunk * 4.0 > 40e6) chunk /= 2;
-  const int64_t blocks = (plan.nseg + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const int threads = kWarpsPerBlock * 32;
+  const int chunk = cfg.chunk > 0 ? std::max(4, cfg.chunk / 4 * 4) : default_chunk(rows_in);
+  const int threads = cfg.threads == 128 ? 128 : 256;
+  const int64_t wpb = threads / 32;
+  const int64_t blocks = (plan.nseg + wpb - 1) / wpb;
   for (int c0 = 0; c0 < K; c0 += chunk) {
     const int kc = std::min(chunk, K - c0);
     const int K4 = kc / 4;
-#define MC_SPMM_ARGS plan.nseg, plan.seg.as<int4>(), idx, val, X + c0, ld_x, K4, out + c0, ld_out, partial
-    if (K4 <= 2) spmm_seg_kernel<16><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-    else if (K4 <= 4) spmm_seg_kernel<8><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-
-    else if (K4 <= 8) spmm_seg_kernel<4><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-    else if (K4 <= 16) spmm_seg_kernel<2><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-    else spmm_seg_kernel<1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-#undef MC_SPMM_ARGS
+    const int G = lane_groups(K4);
+    const int u = cfg.u > 0 ? cfg.u : default_u(G);
+#define MC_SEG_ARGS u, blocks, threads, st, plan.nseg, plan.seg.as<int4>(), idx, val, X + c0, ld_x, K4, out + c0, ld_out, partial
+    if (G == 16) launch_seg<16>(MC_SEG_ARGS);
+    else if (G == 8) launch_seg<8>(MC_SEG_ARGS);
+    else if (G == 4) launch_seg<4>(MC_SEG_ARGS);
+    else if (G == 2) launch_seg<2>(MC_SEG_ARGS);
+    else launch_seg<1>(MC_SEG_ARGS);
+#undef MC_SEG_ARGS
     MC_CHECK_LAUNCH();
     if (plan.nsplit > 0) {
       spmm_fixup_kernel<<<static_cast<unsigned>(plan.nsplit), 128, 0, st>>>(

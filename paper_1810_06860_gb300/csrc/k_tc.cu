@@ -192,11 +192,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
     const float4 *src = reinterpret_cast<const float4 *>(raw[b]);
     float *dh = reinterpret_cast<float *>(hi[b]);
     float *dl = reinterpret_cast<float *>(lo[b]);
+    // a warp takes one 4-column group of a box across its 32 rows (lane = row):
+    // the swizzled reads and the transposed writes are then free of bank conflicts
     for (int q = tid; q < nvec; q += TC_THREADS) {
-      const int box = q >> 8, w = q & 255;  // 256 float4 per box
-      const int r = w >> 3, chunk = (w & 7) ^ (r & 7);
-      const int c0 = box * 32 + chunk * 4;
-      const float4 v = src[q];
+      const int box = q >> 8, k4 = (q >> 5) & 7, r = q & 31;  // 256 float4 per box
+      const int c0 = box * 32 + k4 * 4;
+      const float4 v = src[box * 256 + r * 8 + (k4 ^ (r & 7))];
       const float vals[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {

@@ -21,8 +21,12 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <cstdio>
 #include <limits>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -231,12 +235,96 @@ double spmm_bytes(int64_t nnz, int64_t rows, int64_t rows_in, int K) {
   return 8.0 * nnz + 4.0 * (rows + 1) + 4.0 * (double)(rows_in + rows) * K;
 }
 
+// ---- SpMM launch-shape autotuner ----
+// The first product of a shape class (direction, panel width, log2 of the
+// row, input-row and entry counts) times every candidate launch shape twice
+// with CUDA events on the handle's stream and keeps the fastest for the rest
+// of the process.  The candidates differ only in launch shape, never in the
+// order of any sum, so tuning cannot change a result.  MC_SPMM_TUNE=0 keeps
+// the default shape; MC_SPMM_TUNE_LOG=1 prints the measurements to stderr.
+struct TuneKey {
+  int trans, K, lr, lri, lnnz;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(trans, K, lr, lri, lnnz) < std::tie(o.trans, o.K, o.lr, o.lri, o.lnnz);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, SpmmCfg> g_tune;
+
+bool tune_enabled() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_SPMM_TUNE");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+int ilog2(int64_t x) {
+  int l = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++l;
+  }
+  return l;
+}
+
+template <class F>
+SpmmCfg tuned_cfg(mc_handle h, int trans, int K, int64_t rows, int64_t rows_in, F &&launch) {
+  if (!tune_enabled()) return SpmmCfg{};
+  const TuneKey key{trans, K, ilog2(rows), ilog2(rows_in), ilog2(std::max<int64_t>(h->nnz, 1))};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  const std::vector<SpmmCfg> cand = spmm_candidates(K, rows_in);
+  if (cand.size() < 2) return SpmmCfg{};
+  std::vector<cudaEvent_t> ev(2 * cand.size() * 2 + 1);
+  for (auto &e : ev) MC_CUDA(cudaEventCreate(&e));
+  int q = 0;
+  MC_CUDA(cudaEventRecord(ev[q++], h->stream));
+  for (int rep = 0; rep < 2; ++rep)
+    for (const SpmmCfg &c : cand) {
+      launch(c);
+      MC_CUDA(cudaEventRecord(ev[q++], h->stream));
+    }
+  MC_CUDA(cudaEventSynchronize(ev[q - 1]));
+  std::vector<float> best(cand.size(), 1e30f);
+  for (int rep = 0, t = 1; rep < 2; ++rep)
+    for (size_t i = 0; i < cand.size(); ++i, ++t) {
+      float ms = 0.f;
+      MC_CUDA(cudaEventElapsedTime(&ms, ev[t - 1], ev[t]));
+      best[i] = std::min(best[i], ms);
+    }
+  for (auto &e : ev) cudaEventDestroy(e);
+  size_t bi = 0;
+  for (size_t i = 1; i < cand.size(); ++i)
+    if (best[i] < best[bi]) bi = i;
+  static const bool log = [] {
+    const char *v = std::getenv("MC_SPMM_TUNE_LOG");
+    return v && v[0] == '1';
+  }();
+  if (log) {
+    std::fprintf(stderr, "spmm tune trans=%d K=%d rows=%lld rows_in=%lld nnz=%lld:", trans, K, (long long)rows,
+                 (long long)rows_in, (long long)h->nnz);
+    for (size_t i = 0; i < cand.size(); ++i)
+      std::fprintf(stderr, " [u%d t%d c%d %.1fus]", cand[i].u, cand[i].threads, cand[i].chunk, 1e3 * best[i]);
+    std::fprintf(stderr, " -> %zu\n", bi);
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.emplace(key, cand[bi]);
+  return cand[bi];
+}
+
 // ---- sparse products with the current iterate ----
 void spmm_Y(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_out) {
   fbuf(h, h->sp_part, (size_t)h->plan_r.nslot * K);
+  auto run = [&](const SpmmCfg &c) {
+    spmm(h->stream, h->plan_r, h->ci.as<int>(), h->y.as<float>(), h->n, X, ld_x, K, out, ld_out,
+         h->sp_part.as<float>(), c);
+  };
+  const SpmmCfg cfg = tuned_cfg(h, 0, K, h->m, h->n, run);
   Scope sc(h, MC_T_SPMM, spmm_bytes(h->nnz, h->m, h->n, K), 2.0 * h->nnz * K);
-  spmm(h->stream, h->plan_r, h->ci.as<int>(), h->y.as<float>(), h->n, X, ld_x, K, out, ld_out,
-       h->sp_part.as<float>());
+  run(cfg);
 }
 // Products with bf16 panels (mixed-precision form); X has ld_x = K columns.
 void spmm_Y_bf(mc_handle h, const void *X, int K, float *out, int ld_out) {
@@ -258,9 +346,13 @@ void *bf_panel(mc_handle h, DBuf &b, int64_t rows, int cols, const float *src, i
 
 void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_out) {
   fbuf(h, h->sp_part, (size_t)h->plan_c.nslot * K);
+  auto run = [&](const SpmmCfg &c) {
+    spmm(h->stream, h->plan_c, h->ri.as<int>(), h->yc.as<float>(), h->m, X, ld_x, K, out, ld_out,
+         h->sp_part.as<float>(), c);
+  };
+  const SpmmCfg cfg = tuned_cfg(h, 1, K, h->n, h->m, run);
   Scope sc(h, MC_T_SPMM_T, spmm_bytes(h->nnz, h->n, h->m, K), 2.0 * h->nnz * K);
-  spmm(h->stream, h->plan_c, h->ri.as<int>(), h->yc.as<float>(), h->m, X, ld_x, K, out, ld_out,
-       h->sp_part.as<float>());
+  run(cfg);
 }
 
 // Gram X^T X: the tensor-core kernel (tcgen05, 3xTF32) for tc_min_k() <= K
@@ -276,7 +368,7 @@ bool use_tensor_gram() {
 int tc_min_k() {
   static const int v = [] {
     const char *e = std::getenv("MC_GRAM_TC_MIN_K");
-    return e ? std::max(1, std::atoi(e)) : 32;
+    return e ? std::max(1, std::atoi(e)) : 65;
   }();
   return v;
 }

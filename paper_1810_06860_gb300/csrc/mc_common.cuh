@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/mc.h"
 
@@ -106,8 +107,15 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
 // ld_out multiples of 4 (padded columns must be zero in X).  partial must hold
 // plan.nslot * K floats.
 // rows_in: rows of X (sizes the column chunks so the panel slice stays in L2).
+// Launch shape of the SpMM: gathers in flight per lane group (u), CTA size
+// (threads: 128 or 256) and column-chunk width; 0 selects the default.  None
+// of them changes the order of any sum, so every choice gives the same bits.
+struct SpmmCfg {
+  int u = 0, threads = 0, chunk = 0;
+};
+std::vector<SpmmCfg> spmm_candidates(int K, int64_t rows_in);
 void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, int64_t rows_in,
-          const float *X, int ld_x, int K, float *out, int ld_out, float *partial);
+          const float *X, int ld_x, int K, float *out, int ld_out, float *partial, const SpmmCfg &cfg = SpmmCfg{});
 // As spmm with a bf16 panel X (K, ld_x multiples of 8, K <= 256), float32
 // accumulation and output (mixed-precision form).
 void spmm_bf16(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, const void *Xbf, int ld_x,

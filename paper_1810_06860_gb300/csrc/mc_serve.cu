@@ -344,6 +344,7 @@ mc_status mc_poll(mc_server S, uint64_t job_id, mc_result *out) {
   out->latency_s = std::chrono::duration<double>(J->t_end - J->t_submit).count();
   out->footprint_bytes = J->footprint;
   out->device_bytes_peak = J->dev_peak;
+  out->message = J->error.c_str();
   return J->status == MC_ECANCELLED ? MC_ECANCELLED : MC_OK;
 }
 

@@ -26,8 +26,9 @@ def mc():
     return mc
 
 
-def _prm(mc, o, frac, seed, **kw):
-    return mc.params(tau=5.0 * math.sqrt(o.m * o.n), delta=1.2 / frac, eps=1e-4, i_max=500, seed=seed, **kw)
+def _prm(mc, o, frac, seed):
+    # warm-started Omega (recycle = 3): converges on these jobs in 80-130 iterations
+    return mc.params(tau=5.0 * math.sqrt(o.m * o.n), delta=1.2 / frac, eps=1e-4, i_max=500, seed=seed, recycle=3)
 
 
 def _unobserved_rel_err(o, Us, V):
@@ -40,7 +41,7 @@ def _unobserved_rel_err(o, Us, V):
 
 def test_served_result_same_alone_and_in_mix(mc):
     obs = [mc_synth.lowrank_uniform(m, n, r, frac=f, seed=s) for (m, n, r, f, s) in JOBS]
-    prms = [_prm(mc, o, f, s, recycle=1, i_reuse=50, q_reuse=10) for o, (_, _, _, f, s) in zip(obs, JOBS)]
+    prms = [_prm(mc, o, f, s) for o, (_, _, _, f, s) in zip(obs, JOBS)]
     alone = []
     with mc.Server(max_active=1) as srv:
         for o, p in zip(obs, prms):
@@ -53,7 +54,7 @@ def test_served_result_same_alone_and_in_mix(mc):
     # the jobs ran at the same time: the last admitted started before the first finished
     assert max(r["queue_s"] for r in mix) < min(r["latency_s"] for r in mix)
     for a, b, o in zip(alone, mix, obs):
-        assert a["status"] == 0 and b["status"] == 0, (a["status"], b["status"])
+        assert a["status"] == 0 and b["status"] == 0, (a["status"], b["status"], a["message"], b["message"])
         assert a["iters"] == b["iters"] and a["r"] == b["r"]
         # every kernel is deterministic: bit-identical factors
         assert np.array_equal(a["Us"], b["Us"]) and np.array_equal(a["V"], b["V"])
