@@ -8,6 +8,8 @@
 // All float32; every reduction runs in a fixed order (deterministic).
 #include "mc_common.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cfloat>
 #include <mutex>
@@ -634,6 +636,185 @@ __global__ void select_cols_kernel(int K, const float *__restrict__ W, int ld_w,
   }
 }
 
+// ===================================== narrow block orthonormalisation ====
+// One cooperative kernel for a whole Krylov block of width K <= 32 (the
+// narrow blocks of the SVT iteration): optional column norms before the
+// projection (the dependence test), two projections against the earlier
+// blocks Qp (X -= Qp (Qp^T X)), then three CholeskyQR passes (shifted, plain,
+// plain), exactly the sequence of the separate kernels.  Each CTA keeps its
+// rows of X and Qp in shared memory for the whole sequence; every reduction
+// over rows is per-CTA partials, a grid barrier, a fixed-order sum split
+// across the CTAs, and a second barrier.  The K x K Cholesky-inverse is
+// repeated by every CTA (it is tiny), so its result needs no barrier.
+constexpr int ON_THREADS = 256;
+constexpr int ON_MAXK = 32;
+
+struct OrthNarrowArgs {
+  int64_t R, rows_per;
+  int K, cols, ldx, ldq, ldo, use_ref;
+  float *X;          // R x K (clobbered)
+  const float *Qp;   // R x cols
+  float *out;        // R x K
+  float *part;       // nblk x max(cols K + K, K K)
+  float *fin;        // cols K + K + K K
+  float shift_rel, ref_tol;
+};
+
+// sum over the CTAs' partials of entries [0, count): a warp per entry, lane l
+// adds partials l, l + 32, ... and the lanes' sums meet in a fixed shuffle tree
+__device__ __forceinline__ void on_reduce(const OrthNarrowArgs &a, int count, int stride, float *dst) {
+  const int nb = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (ON_THREADS / 32) + (threadIdx.x >> 5), nw = nb * (ON_THREADS / 32);
+  for (int e = gw; e < count; e += nw) {
+    float acc = 0.f;
+    for (int b = lane; b < nb; b += 32) acc += a.part[(int64_t)b * stride + e];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) dst[e] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(ON_THREADS, 1) orth_narrow_kernel(OrthNarrowArgs a) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) float onsm[];
+  const int K = a.K, cols = a.cols, tid = threadIdx.x;
+  const int ldh = K + 1;           // row padding against bank conflicts
+  const int64_t r0 = blockIdx.x * a.rows_per;
+  const int64_t r1 = a.R < r0 + a.rows_per ? a.R : r0 + a.rows_per;
+  const int nr = r1 > r0 ? static_cast<int>(r1 - r0) : 0;
+  float *Hs = onsm;                                   // nr x ldh
+  float *Qs = Hs + (size_t)a.rows_per * ldh;          // nr x cols
+  float *Ms = Qs + (size_t)a.rows_per * cols;         // cols x K (C) or K x K (G)
+  float *Ls = Ms + (size_t)max(cols, K) * K;          // K x (K+1): Cholesky factor
+  float *Bs = Ls + (size_t)K * (K + 1);               // K x (K+1): running inverse
+  float *fl = Bs + (size_t)K * (K + 1);               // K flags
+  float *refs = fl + K;                               // K column norms^2
+  const int stride = max(cols * K + K, K * K);
+  float *fin_C = a.fin, *fin_G = a.fin + cols * K + K;
+
+  for (int t = tid; t < nr * K; t += ON_THREADS) {
+    const int r = t / K, c = t % K;
+    Hs[r * ldh + c] = a.X[(r0 + r) * a.ldx + c];
+  }
+  for (int t = tid; t < nr * cols; t += ON_THREADS) {
+    const int r = t / cols, c = t % cols;
+    Qs[r * cols + c] = a.Qp[(r0 + r) * a.ldq + c];
+  }
+  __syncthreads();
+
+  // X -= Qp (Qp^T X), twice; the column norms^2 before the projection (the
+  // dependence test of the first pass) ride along with the first product
+  const int nref = a.use_ref ? K : 0;
+  for (int rep = 0; rep < 2 && cols > 0; ++rep) {
+    const int cnt = cols * K + (rep == 0 ? nref : 0);
+    for (int o = tid; o < cnt; o += ON_THREADS) {
+      float acc = 0.f;
+      if (o < cols * K) {
+        const int i = o / K, j = o % K;
+        for (int r = 0; r < nr; ++r) acc = fmaf(Qs[r * cols + i], Hs[r * ldh + j], acc);
+      } else {
+        const int c = o - cols * K;
+        for (int r = 0; r < nr; ++r) acc = fmaf(Hs[r * ldh + c], Hs[r * ldh + c], acc);
+      }
+      a.part[(int64_t)blockIdx.x * stride + o] = acc;
+    }
+    grid.sync();
+    on_reduce(a, cnt, stride, fin_C);
+    grid.sync();
+    for (int o = tid; o < cols * K; o += ON_THREADS) Ms[o] = fin_C[o];
+    if (rep == 0)
+      for (int c = tid; c < nref; c += ON_THREADS) refs[c] = fin_C[cols * K + c];
+    __syncthreads();
+    for (int t = tid; t < nr * K; t += ON_THREADS) {
+      const int r = t / K, j = t % K;
+      float acc = 0.f;
+      for (int i = 0; i < cols; ++i) acc = fmaf(Qs[r * cols + i], Ms[i * K + j], acc);
+      Hs[r * ldh + j] -= acc;
+    }
+    __syncthreads();
+  }
+
+  // three CholeskyQR passes: X <- X R^{-1} with X^T X + shift I = R^T R
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int o = tid; o < K * K; o += ON_THREADS) {
+      const int i = o / K, j = o % K;
+      float acc = 0.f;
+      if (i <= j)
+        for (int r = 0; r < nr; ++r) acc = fmaf(Hs[r * ldh + i], Hs[r * ldh + j], acc);
+      a.part[(int64_t)blockIdx.x * stride + o] = acc;
+    }
+    grid.sync();
+    on_reduce(a, K * K, stride, fin_G);
+    grid.sync();
+    // G (upper triangle reduced; mirrored) -> L L^T and L^{-1}, as chol_inv
+    __shared__ float s_tr, s_max;
+    if (tid == 0) {
+      float tr = 0.f, mx = 0.f;
+      for (int i = 0; i < K; ++i) {
+        tr += fin_G[i * K + i];
+        mx = fmaxf(mx, fin_G[i * K + i]);
+      }
+      s_tr = tr;
+      s_max = mx;
+    }
+    for (int i = tid; i < K; i += ON_THREADS)
+      fl[i] = (pass == 0 && a.use_ref && !(fin_G[i * K + i] > a.ref_tol * refs[i])) ? 0.f : 1.f;
+    __syncthreads();
+    const float shift = (pass == 0 ? a.shift_rel : 0.f) * s_tr / K;
+    const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
+    for (int t = tid; t < K * K; t += ON_THREADS) {
+      const int i = t / K, j = t % K;
+      const bool live = fl[i] != 0.f && fl[j] != 0.f;
+      Ls[i * (K + 1) + j] = (j <= i && live) ? fin_G[j * K + i] + (i == j ? shift : 0.f) : 0.f;
+      Bs[i * (K + 1) + j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    const int wid = tid >> 5, lane = tid & 31;
+    for (int j = 0; j < K; ++j) {
+      const float d = Ls[j * (K + 1) + j];
+      const bool keep = d > drop;
+      const float inv = keep ? rsqrtf(d) : 0.f;
+      for (int i = j + 1 + tid; i < K; i += ON_THREADS) Ls[i * (K + 1) + j] *= inv;
+      for (int c = tid; c <= j; c += ON_THREADS) Bs[j * (K + 1) + c] *= inv;
+      if (tid == 0 && !keep) fl[j] = 0.f;
+      __syncthreads();
+      if (keep)
+        for (int r = j + 1 + wid; r < K; r += ON_THREADS / 32) {
+          const float lr = Ls[r * (K + 1) + j];
+          for (int b = lane; b <= r; b += 32) {
+            if (b <= j) Bs[r * (K + 1) + b] -= lr * Bs[j * (K + 1) + b];
+            else Ls[r * (K + 1) + b] -= lr * Ls[b * (K + 1) + j];
+          }
+        }
+      __syncthreads();
+    }
+    // X <- X R^{-1}, R^{-1}[l][c] = L^{-1}[c][l] (kept l, c only), a thread per row
+    for (int r = tid; r < nr; r += ON_THREADS) {
+      float h[ON_MAXK];
+#pragma unroll
+      for (int l = 0; l < ON_MAXK; ++l) h[l] = (l < K && fl[l] != 0.f) ? Hs[r * ldh + l] : 0.f;
+#pragma unroll
+      for (int c = 0; c < ON_MAXK; ++c) {
+        if (c < K) {
+          float acc = 0.f;
+          if (fl[c] != 0.f) {
+#pragma unroll
+            for (int l = 0; l <= c; ++l) acc = fmaf(h[l], Bs[c * (K + 1) + l], acc);
+          }
+          Hs[r * ldh + c] = acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < nr * K; t += ON_THREADS) {
+    const int r = t / K, c = t % K;
+    a.out[(r0 + r) * a.ldo + c] = Hs[r * ldh + c];
+  }
+}
+
 }  // namespace
 
 // ================================================================ launchers ==
@@ -770,6 +951,68 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
   const int threads = K <= 128 ? 256 : 1024;
   chol_inv_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, x_sm ? 1 : 0);
   MC_CHECK_LAUNCH();
+}
+
+static int64_t on_stride(int K, int cols) { return std::max<int64_t>((int64_t)cols * K + K, (int64_t)K * K); }
+
+size_t orth_narrow_scratch_floats(int64_t R, int K, int cols) {
+  (void)R;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  const int64_t nb_max = (int64_t)std::max(sms, 1) * 4;
+  return (size_t)(nb_max * on_stride(K, cols) + (int64_t)cols * K + K + (int64_t)K * K + 64);
+}
+
+static size_t on_smem(int64_t rows_per, int K, int cols) {
+  return sizeof(float) * ((size_t)rows_per * (K + 1) + (size_t)rows_per * cols + (size_t)std::max(cols, K) * K +
+                          2 * (size_t)K * (K + 1) + 2 * (size_t)K);
+}
+
+bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
+                 int ldo, const float *ref_unused, bool use_ref, float shift_rel, float ref_tol, float *scratch) {
+  (void)ref_unused;
+  if (K < 1 || K > ON_MAXK || R < 1 || cols < 0) return false;
+  int dev = 0, sms = 0, coop = 0;
+  MC_CUDA(cudaGetDevice(&dev));
+  MC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  MC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop || sms <= 0) return false;
+  MC_CUDA(cudaFuncSetAttribute(orth_narrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  // CTAs: one to four per SM, at least 32 rows each, the rows and the
+  // panel slices of a CTA in at most 220 KB / CTAs-per-SM of shared memory
+  for (int per_sm = 1; per_sm <= 4; ++per_sm) {
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (R + 31) / 32));
+    const int64_t rows_per = (R + nb - 1) / nb;
+    const size_t smem = on_smem(rows_per, K, cols);
+    if (smem > (size_t)220 * 1024 / per_sm) continue;
+    int occ = 0;
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, orth_narrow_kernel, ON_THREADS, smem));
+    if ((int64_t)occ * sms < nb) continue;
+    const int64_t stride = on_stride(K, cols);
+    OrthNarrowArgs a{};
+    a.R = R;
+    a.rows_per = rows_per;
+    a.K = K;
+    a.cols = cols;
+    a.ldx = ldx;
+    a.ldq = ldq;
+    a.ldo = ldo;
+    a.use_ref = use_ref ? 1 : 0;
+    a.X = X;
+    a.Qp = Qp;
+    a.out = out;
+    a.part = scratch;
+    a.fin = scratch + nb * stride;
+    a.shift_rel = shift_rel;
+    a.ref_tol = ref_tol;
+    void *args[] = {&a};
+    MC_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(orth_narrow_kernel), dim3((unsigned)nb),
+                                        dim3(ON_THREADS), args, smem, st));
+    count_launch();
+    return true;
+  }
+  return false;
 }
 
 // ===================================================== allocation-free Gram ==

@@ -2,12 +2,16 @@
 // matrix, the eig() step of eigSVD (Alg. 3 step 2) applied to the Gram of
 // B^T in rSVD-PI / rSVD-BKI (Alg. 4/5).
 //
-// Kernel 1 (one block of 1024 threads): Householder reduction to tridiagonal
-//   form T = Q^T A Q.  The packed lower triangle lives in shared memory; the
+// Kernel 1 (one block of 1024 threads; 512 above K = 513): Householder
+//   reduction to tridiagonal form T = Q^T A Q.  The packed lower triangle
+//   lives in shared memory while it fits, else in global memory (L2); the
 //   symmetric matrix-vector product reads every stored element once, row by
-//   row (a warp per row, lanes along the row), keeping the transposed
-//   contributions in per-lane registers, so all accesses are bank-conflict
-//   free.  Four barriers per column.  The reflectors go to global memory.
+//   row (a warp per row, lanes along the row: coalesced, bank-conflict free),
+//   keeping the transposed contributions in per-lane registers (8, 16 or 32
+//   per lane for K up to 257, 513, 1025).  Four barriers per column.  The
+//   reflectors go to global memory.
+//   Sub-columns whose squared norm is below (eps max|A|)^2 are left as they
+//   are (rounding residue of a rank-deficient Gram).
 // Kernel 2 (one block of 1024 threads):
 //   - Sturm-count multisection for the kw largest eigenvalues of T;
 //   - inverse iteration, one thread per eigenvalue (pivoted tridiagonal LU,
@@ -21,6 +25,8 @@
 // Everything is float32; every reduction has a fixed order.
 #include "mc_common.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cfloat>
 
@@ -30,7 +36,6 @@ namespace {
 constexpr int EIG_THREADS = 1024;
 constexpr int NW = EIG_THREADS / 32;
 constexpr size_t EIG_SMEM = 220 * 1024;
-constexpr int TRI_FAST_MAX = 256;  // transposed contributions in registers up to this size
 constexpr int HV_CHUNK = 16;       // reflectors staged per back-transformation chunk
 
 __device__ __forceinline__ int pk(int r, int c) { return r * (r + 1) / 2 + c; }  // r >= c
@@ -58,37 +63,69 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 }
 
 // --------------------------------------------------------------- kernel 1 --
-__global__ void __launch_bounds__(EIG_THREADS, 1)
+// PPR transposed-contribution registers per lane cover columns up to 32 PPR;
+// THREADS threads (fewer for the widest case, to leave registers for them).
+template <int NWT>
+__device__ __forceinline__ float block_sum_n(float v, float *red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll 8
+  for (int q = 0; q < NWT; ++q) t += red[q];
+  return t;
+}
+
+template <int PPR, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 eig_tridiag_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d, float *__restrict__ g_e,
                    float *__restrict__ g_beta, float *__restrict__ Hv, float *__restrict__ gP, int p_in_smem) {
+  constexpr int NWT = THREADS / 32;
+  constexpr int TMAX = 32 * PPR;
   extern __shared__ __align__(16) float sm[];
   __shared__ float red[2][32];
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const bool fast = K <= TRI_FAST_MAX + 1;
   float *vv = sm;                 // K
   float *pw = vv + K;             // K
   float *prow = pw + K;           // K
   float *dd = prow + K;           // K
-  float *ppw = dd + K;            // NW x TRI_FAST_MAX (fast path)
-  float *P = p_in_smem ? ppw + (fast ? NW * TRI_FAST_MAX : 0) : gP;
+  float *ppw = dd + K;            // NWT x TMAX
+  float *P = p_in_smem ? ppw + NWT * TMAX : gP;
 
-  for (int r = wid; r < K; r += NW)
-    for (int c = lane; c <= r; c += 32) P[pk(r, c)] = A[(int64_t)r * lda + c];
+  float amax_part = 0.f;
+  for (int r = wid; r < K; r += NWT)
+    for (int c = lane; c <= r; c += 32) {
+      const float x = A[(int64_t)r * lda + c];
+      P[pk(r, c)] = x;
+      amax_part = fmaxf(amax_part, fabsf(x));
+    }
+  // largest magnitude: a sub-column whose squared norm is below (eps |A|)^2 is
+  // rounding residue (the trailing block of a rank-deficient Gram) and is not
+  // reflected; reflecting it would divide by a denormal and overflow
+  __shared__ float s_amax[NWT];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax_part = fmaxf(amax_part, __shfl_xor_sync(0xffffffffu, amax_part, off));
+  if (lane == 0) s_amax[wid] = amax_part;
   __syncthreads();
+  float amax = 0.f;
+#pragma unroll 8
+  for (int q = 0; q < NWT; ++q) amax = fmaxf(amax, s_amax[q]);
+  const float sig_floor = fmaxf((FLT_EPSILON * amax) * (FLT_EPSILON * amax), 1e-37f);
   int rb = 0;  // alternating reduction buffer
   for (int i = 0; i + 2 < K; ++i) {
     const int n = K - 1 - i;
     float part = 0.f;
-    for (int a = 1 + tid; a < n; a += EIG_THREADS) {
+    for (int a = 1 + tid; a < n; a += THREADS) {
       const float x = P[pk(i + 1 + a, i)];
       vv[a] = x;
       part += x * x;
     }
-    const float sigma = block_sum1(part, red[rb]);
+    const float sigma = block_sum_n<NWT>(part, red[rb]);
     rb ^= 1;
     const float x0 = P[pk(i + 1, i)];
     float bt = 0.f, alpha = x0, v0 = 0.f;
-    if (sigma > 0.f) {
+    if (sigma > sig_floor) {
       const float mu = sqrtf(x0 * x0 + sigma);
       alpha = x0 <= 0.f ? mu : -mu;
       v0 = x0 - alpha;
@@ -100,75 +137,53 @@ eig_tridiag_kernel(int K, const float *__restrict__ A, int lda, float *__restric
       g_beta[i] = bt;
       Hv[(int64_t)i * K] = v0;
     }
-    for (int a = 1 + tid; a < n; a += EIG_THREADS) Hv[(int64_t)i * K + a] = vv[a];
+    for (int a = 1 + tid; a < n; a += THREADS) Hv[(int64_t)i * K + a] = vv[a];
     if (bt == 0.f) {
       __syncthreads();
       continue;
     }
-    float vp = 0.f;
-    if (fast) {
-      // p = A' v: warp per row a, lanes along the row; the row's transposed
-      // contributions A'(a,b) v_a (b < a) accumulate in pp[] of lane b % 32
-      float pp[TRI_FAST_MAX / 32];
+    // p = A' v: warp per row a, lanes along the row (coalesced); the row's
+    // transposed contributions A'(a,b) v_a (b < a) accumulate in pp[] of
+    // lane b % 32, so the packed triangle is read once, by rows
+    float pp[PPR];
 #pragma unroll
-      for (int j = 0; j < TRI_FAST_MAX / 32; ++j) pp[j] = 0.f;
-      for (int a = wid; a < n; a += NW) {
-        const float va = a == 0 ? v0 : vv[a];
-        const float *row = P + pk(i + 1 + a, i + 1);
-        float acc = 0.f;
+    for (int j = 0; j < PPR; ++j) pp[j] = 0.f;
+    for (int a = wid; a < n; a += NWT) {
+      const float va = a == 0 ? v0 : vv[a];
+      const float *row = P + pk(i + 1 + a, i + 1);
+      float acc = 0.f;
 #pragma unroll
-        for (int j = 0; j < TRI_FAST_MAX / 32; ++j) {
-          const int b = lane + 32 * j;
-          if (b <= a) {
-            const float x = row[b];
-            acc = fmaf(x, b == 0 ? v0 : vv[b], acc);
-            if (b < a) pp[j] = fmaf(x, va, pp[j]);
-          }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) prow[a] = acc;
-      }
-#pragma unroll
-      for (int j = 0; j < TRI_FAST_MAX / 32; ++j) {
+      for (int j = 0; j < PPR; ++j) {
         const int b = lane + 32 * j;
-        if (b < n) ppw[wid * TRI_FAST_MAX + b] = pp[j];
-      }
-      __syncthreads();
-      for (int b = tid; b < n; b += EIG_THREADS) {
-        float acc = prow[b];
-#pragma unroll 8
-        for (int w = 0; w < NW; ++w) acc += ppw[w * TRI_FAST_MAX + b];
-        const float pb = bt * acc;
-        pw[b] = pb;
-        vp = fmaf(b == 0 ? v0 : vv[b], pb, vp);
-      }
-    } else {
-      // large K: row groups read rows and (strided) columns of the packed triangle
-      int tpr = 32;
-      while (tpr > 1 && n * tpr > EIG_THREADS) tpr >>= 1;
-      const int rows_per_pass = EIG_THREADS / tpr;
-      for (int a0 = 0; a0 < n; a0 += rows_per_pass) {
-        const int a = a0 + tid / tpr, q = tid % tpr;
-        float sacc = 0.f;
-        if (a < n) {
-          const int ra = i + 1 + a;
-          const float *row = P + pk(ra, i + 1);
-          for (int b = q; b <= a; b += tpr) sacc += row[b] * (b == 0 ? v0 : vv[b]);
-          for (int b = a + 1 + q; b < n; b += tpr) sacc += P[pk(i + 1 + b, ra)] * vv[b];
-        }
-        for (int off = tpr >> 1; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-        if (a < n && q == 0) {
-          const float pa = bt * sacc;
-          pw[a] = pa;
-          vp = fmaf(a == 0 ? v0 : vv[a], pa, vp);
+        if (b <= a) {
+          const float x = row[b];
+          acc = fmaf(x, b == 0 ? v0 : vv[b], acc);
+          if (b < a) pp[j] = fmaf(x, va, pp[j]);
         }
       }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) prow[a] = acc;
     }
-    const float c = 0.5f * bt * block_sum1(vp, red[rb]);
+#pragma unroll
+    for (int j = 0; j < PPR; ++j) {
+      const int b = lane + 32 * j;
+      if (b < n) ppw[wid * TMAX + b] = pp[j];
+    }
+    __syncthreads();
+    float vp = 0.f;
+    for (int b = tid; b < n; b += THREADS) {
+      float acc = prow[b];
+#pragma unroll 8
+      for (int w = 0; w < NWT; ++w) acc += ppw[w * TMAX + b];
+      const float pb = bt * acc;
+      pw[b] = pb;
+      vp = fmaf(b == 0 ? v0 : vv[b], pb, vp);
+    }
+    const float c = 0.5f * bt * block_sum_n<NWT>(vp, red[rb]);
     rb ^= 1;
     // A' -= v w^T + w v^T with w = p - c v, lower triangle, warp per row
-    for (int a = wid; a < n; a += NW) {
+    for (int a = wid; a < n; a += NWT) {
       const float va = a == 0 ? v0 : vv[a];
       const float wa = pw[a] - c * va;
       float *row = P + pk(i + 1 + a, i + 1);
@@ -191,7 +206,138 @@ eig_tridiag_kernel(int K, const float *__restrict__ A, int lda, float *__restric
     g_beta[K - 1] = 0.f;
   }
   __syncthreads();
-  for (int a = tid; a < K; a += EIG_THREADS) g_d[a] = dd[a];
+  for (int a = tid; a < K; a += THREADS) g_d[a] = dd[a];
+}
+
+// ------------------------------------------------- kernel 1, many CTAs --
+// The same reduction for K > 256, where one SM's bandwidth to the matrix is
+// the limit: a cooperative grid keeps the full symmetric matrix in global
+// memory (L2).  Every CTA computes the Householder vector of the current
+// column itself (same data, same order, same result), the warps of the grid
+// share the rows of the trailing block for the product p = A v and for the
+// rank-2 update, and two grid barriers per column separate the phases.  The
+// update term v_r w_b + w_r v_b is formed with unfused roundings, so entry
+// (r, b) and entry (b, r) stay bit-equal.
+constexpr int CT_THREADS = 256;
+__global__ void __launch_bounds__(CT_THREADS)
+eig_tridiag_coop_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ Af, float *__restrict__ g_d,
+                        float *__restrict__ g_e, float *__restrict__ g_beta, float *__restrict__ Hv,
+                        float *__restrict__ g_p, float *__restrict__ g_part) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) float ctm[];
+  float *v = ctm;      // K
+  float *w = v + K;    // K
+  __shared__ float red[2][CT_THREADS / 32];
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int nb = gridDim.x;
+  const int64_t gt = (int64_t)blockIdx.x * CT_THREADS + tid, gstride = (int64_t)nb * CT_THREADS;
+  // full symmetric copy from the lower triangle, and the largest magnitude
+  float amax_part = 0.f;
+  for (int64_t t = gt; t < (int64_t)K * K; t += gstride) {
+    const int r = static_cast<int>(t / K), c = static_cast<int>(t % K);
+    const float x = r >= c ? A[(int64_t)r * lda + c] : A[(int64_t)c * lda + r];
+    Af[t] = x;
+    amax_part = fmaxf(amax_part, fabsf(x));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax_part = fmaxf(amax_part, __shfl_xor_sync(0xffffffffu, amax_part, off));
+  if (lane == 0) red[0][wid] = amax_part;
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int q = 0; q < CT_THREADS / 32; ++q) m = fmaxf(m, red[0][q]);
+    g_part[blockIdx.x] = m;
+  }
+  grid.sync();
+  float amax = 0.f;
+  for (int b = 0; b < nb; ++b) amax = fmaxf(amax, g_part[b]);
+  const float sig_floor = fmaxf((FLT_EPSILON * amax) * (FLT_EPSILON * amax), 1e-37f);
+  grid.sync();  // every CTA has read the maxima before the partials are reused
+  const int gw = blockIdx.x * (CT_THREADS / 32) + wid, nwarps = nb * (CT_THREADS / 32);
+  int rb = 0;
+  for (int i = 0; i + 2 < K; ++i) {
+    const int n = K - 1 - i;
+    // Householder vector of column i (every CTA)
+    float part = 0.f;
+    for (int a = tid; a < n; a += CT_THREADS) {
+      const float x = Af[(int64_t)(i + 1 + a) * K + i];
+      v[a] = x;
+      if (a >= 1) part += x * x;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (lane == 0) red[rb][wid] = part;
+    __syncthreads();
+    float sigma = 0.f;
+#pragma unroll
+    for (int q = 0; q < CT_THREADS / 32; ++q) sigma += red[rb][q];
+    rb ^= 1;
+    const float x0 = v[0];
+    float bt = 0.f, alpha = x0, v0 = 0.f;
+    if (sigma > sig_floor) {
+      const float mu = sqrtf(x0 * x0 + sigma);
+      alpha = x0 <= 0.f ? mu : -mu;
+      v0 = x0 - alpha;
+      bt = 2.0f / (v0 * v0 + sigma);
+    }
+    if (blockIdx.x == 0) {
+      if (tid == 0) {
+        g_d[i] = Af[(int64_t)i * K + i];
+        g_e[i] = alpha;
+        g_beta[i] = bt;
+        Hv[(int64_t)i * K] = v0;
+      }
+      for (int a = 1 + tid; a < n; a += CT_THREADS) Hv[(int64_t)i * K + a] = v[a];
+    }
+    __syncthreads();
+    if (tid == 0) v[0] = v0;
+    __syncthreads();
+    if (bt == 0.f) continue;  // uniform over the grid: no update, no barrier
+    // p = bt A' v, a warp per row of the trailing block
+    float vp = 0.f;
+    for (int a = gw; a < n; a += nwarps) {
+      const float *row = Af + (int64_t)(i + 1 + a) * K + (i + 1);
+      float acc = 0.f;
+      for (int b = lane; b < n; b += 32) acc = fmaf(row[b], v[b], acc);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      const float pa = bt * acc;
+      if (lane == 0) g_p[a] = pa;
+      vp = fmaf(v[a], pa, vp);  // the same in every lane of the warp
+    }
+    if (lane == 0) red[rb][wid] = vp;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int q = 0; q < CT_THREADS / 32; ++q) t += red[rb][q];
+      g_part[blockIdx.x] = t;
+    }
+    rb ^= 1;
+    grid.sync();
+    float vps = 0.f;
+    for (int b = 0; b < nb; ++b) vps += g_part[b];
+    const float c = 0.5f * bt * vps;
+    for (int a = tid; a < n; a += CT_THREADS) w[a] = g_p[a] - c * v[a];
+    __syncthreads();
+    // A' -= v w^T + w v^T, a warp per row
+    for (int a = gw; a < n; a += nwarps) {
+      float *row = Af + (int64_t)(i + 1 + a) * K + (i + 1);
+      const float va = v[a], wa = w[a];
+      for (int b = lane; b < n; b += 32) row[b] -= __fadd_rn(__fmul_rn(va, w[b]), __fmul_rn(wa, v[b]));
+    }
+    grid.sync();
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (K >= 2) {
+      g_d[K - 2] = Af[(int64_t)(K - 2) * K + (K - 2)];
+      g_e[K - 2] = Af[(int64_t)(K - 1) * K + (K - 2)];
+      g_beta[K - 2] = 0.f;
+    }
+    g_d[K - 1] = Af[(int64_t)(K - 1) * K + (K - 1)];
+    g_e[K - 1] = 0.f;
+    g_beta[K - 1] = 0.f;
+  }
 }
 
 // --------------------------------------------------------------- kernel 2 --
@@ -384,8 +530,14 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
           x1 = xx;
           nrm = fmaxf(nrm, fabsf(xx));
         }
-        const float sc = nrm > 0.f ? 1.0f / nrm : 1.0f;
-        for (int a = 0; a < K; ++a) Z[(int64_t)a * ldz + t] *= sc;
+        // an overflowed solve restarts from the scaled start vector
+        const bool fin = nrm <= FLT_MAX;
+        const float sc = fin ? (nrm > 0.f ? 1.0f / nrm : 1.0f) : 0.f;
+        for (int a = 0; a < K; ++a) {
+          const float z = Z[(int64_t)a * ldz + t];
+          Z[(int64_t)a * ldz + t] =
+              fin ? z * sc : (float)(hash32((uint32_t)(a * 7919 + t * 104729 + 12345)) >> 8) * (1.0f / 16777216.0f) - 0.5f;
+        }
       }
     }
     __syncthreads();
@@ -471,6 +623,8 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
 
 // ------------------------------------------------------------------ plans --
 struct EigPlan {
+  int coop;          // many-CTA reduction (K > 256, cooperative launch available)
+  int64_t g_af, g_pv, g_part;
   int p_in_smem;
   size_t tri_smem;
   VecLayout vl;
@@ -478,10 +632,20 @@ struct EigPlan {
   int64_t g_d, g_e, g_beta, g_hv, g_p, g_total;  // float offsets in the work area
 };
 
+// Tridiagonalisation variant for K: registers per lane and threads.
+struct TriCfg {
+  int ppr, threads;
+};
+TriCfg tri_cfg(int K) {
+  if (K - 1 <= 256) return {8, 1024};
+  if (K - 1 <= 512) return {16, 1024};
+  return {32, 512};
+}
+
 EigPlan eig_plan(int K, int kw) {
   EigPlan pl{};
-  const bool fast = K <= TRI_FAST_MAX + 1;
-  const size_t tri_fixed = sizeof(float) * (4 * (size_t)K + (fast ? (size_t)NW * TRI_FAST_MAX : 0));
+  const TriCfg tc = tri_cfg(K);
+  const size_t tri_fixed = sizeof(float) * (4 * (size_t)K + (size_t)(tc.threads / 32) * 32 * tc.ppr);
   const size_t pbytes = sizeof(float) * ((size_t)K * (K + 1) / 2);
   pl.p_in_smem = tri_fixed + pbytes <= EIG_SMEM;
   pl.tri_smem = tri_fixed + (pl.p_in_smem ? pbytes : 0);
@@ -496,6 +660,13 @@ EigPlan eig_plan(int K, int kw) {
   off += round_up((int64_t)K * K, 64);
   pl.g_p = off;
   off += pl.p_in_smem ? 0 : round_up((int64_t)K * (K + 1) / 2, 64);
+  pl.coop = K > 256;
+  pl.g_af = off;
+  off += pl.coop ? round_up((int64_t)K * K, 64) : 0;
+  pl.g_pv = off;
+  off += pl.coop ? round_up(K, 64) : 0;
+  pl.g_part = off;
+  off += pl.coop ? 1024 : 0;
   VecLayout vl{};
   vl.ldz = kw | 1;
   const size_t vfixed = sizeof(float) * (3 * (size_t)K + 4 * (size_t)kw + NW * 32 + (size_t)HV_CHUNK * K) + 16;
@@ -525,10 +696,42 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   const EigPlan pl = eig_plan(K, kw);
   MC_REQUIRE(pl.vec_smem <= EIG_SMEM && pl.tri_smem <= EIG_SMEM, "eig_topk: shared-memory plan does not fit");
   float *gw = static_cast<float *>(work);
-  MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
   MC_CUDA(cudaFuncSetAttribute(eig_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
-  eig_tridiag_kernel<<<1, EIG_THREADS, pl.tri_smem, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
-                                                         gw + pl.g_hv, gw + pl.g_p, pl.p_in_smem);
+  const TriCfg tc = tri_cfg(K);
+  bool done = false;
+  if (pl.coop) {
+    int dev = 0, sms = 0, coop = 0, occ = 0;
+    MC_CUDA(cudaGetDevice(&dev));
+    MC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    const size_t smem = sizeof(float) * 2 * (size_t)K;
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eig_tridiag_coop_kernel, CT_THREADS, smem));
+    const int nb = std::min(std::min(sms, (K + 7) / 8), 1024);
+    if (coop && occ >= 1 && nb >= 1) {
+      float *Af = gw + pl.g_af, *gd = gw + pl.g_d, *ge = gw + pl.g_e, *gb = gw + pl.g_beta, *hv = gw + pl.g_hv;
+      float *gp = gw + pl.g_pv, *gpart = gw + pl.g_part;
+      int Kv = K, ldav = lda;
+      const float *Av = A;
+      void *args[] = {&Kv, &Av, &ldav, &Af, &gd, &ge, &gb, &hv, &gp, &gpart};
+      MC_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(eig_tridiag_coop_kernel), dim3(nb),
+                                          dim3(CT_THREADS), args, smem, st));
+      count_launch();
+      done = true;
+    }
+  }
+#define MC_TRI_ARGS K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta, gw + pl.g_hv, gw + pl.g_p, pl.p_in_smem
+  if (done) {
+  } else if (tc.ppr == 8) {
+    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+    eig_tridiag_kernel<8, 1024><<<1, 1024, pl.tri_smem, st>>>(MC_TRI_ARGS);
+  } else if (tc.ppr == 16) {
+    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<16, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+    eig_tridiag_kernel<16, 1024><<<1, 1024, pl.tri_smem, st>>>(MC_TRI_ARGS);
+  } else {
+    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<32, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+    eig_tridiag_kernel<32, 512><<<1, 512, pl.tri_smem, st>>>(MC_TRI_ARGS);
+  }
+#undef MC_TRI_ARGS
   MC_CHECK_LAUNCH();
   eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                          gw + pl.g_hv, lam, W, ld_w, gw, pl.vl);

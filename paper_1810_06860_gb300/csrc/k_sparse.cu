@@ -23,7 +23,7 @@
 namespace mc {
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
+constexpr int kWarpsPerBlock = 4;  // bf16 products: 128-thread CTAs (the faster shape measured)
 
 // ---------------------------------------------------------------- ingest ----
 __global__ void rowptr_check_kernel(int64_t m, int64_t nnz, const int64_t *__restrict__ rp64,
@@ -185,7 +185,7 @@ spmm_seg_bf16_kernel(int64_t nseg, const int4 *__restrict__ segs, const int *__r
                      const float *__restrict__ val, const __nv_bfloat16 *__restrict__ X, int ld_x, int K8,
                      float *__restrict__ out, int ld_out, float *__restrict__ partial) {
   constexpr int L = 32 / G;
-  constexpr int U = G >= 8 ? 1 : (G >= 2 ? 2 : 4);
+  constexpr int U = 1;  // one gather in flight per group (the faster choice measured)
   const int lane = threadIdx.x & 31;
   const int64_t seg = blockIdx.x * (int64_t)kWarpsPerBlock + (threadIdx.x >> 5);
   if (seg >= nseg) return;
@@ -486,18 +486,19 @@ void launch_seg(int u, int64_t blocks, int threads, cudaStream_t st, int64_t nse
 }
 }  // namespace
 
+// Lane groups of a product: from the widest chunk the default chunking uses,
+// so that every chunking the tuner tries fits the same groups.
+int spmm_groups(int K, int64_t rows_in) { return lane_groups(std::min(K, default_chunk(rows_in)) / 4); }
+
 std::vector<SpmmCfg> spmm_candidates(int K, int64_t rows_in) {
-  const int G = lane_groups(std::min(K, 128) / 4);
+  const int G = spmm_groups(K, rows_in);
   const int dc = default_chunk(rows_in);
   std::vector<SpmmCfg> c;
   for (int u : {1, 2, 4}) {
     if (G * u > 32) continue;
     for (int threads : {128, 256}) c.push_back({u, threads, dc});
   }
-  if (K > 32) {
-    const int alt = dc >= 64 ? dc / 2 : dc * 2;
-    c.push_back({default_u(G), 256, alt});
-  }
+  if (K > 32) c.push_back({1, 128, dc / 2});  // narrower chunks only: wider ones would need other groups
   return c;
 }
 
@@ -506,15 +507,20 @@ void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val
   if (plan.nseg == 0 || K <= 0) return;
   MC_REQUIRE(K % 4 == 0 && ld_x % 4 == 0 && ld_out % 4 == 0, "spmm: K and leading dims must be multiples of 4");
   MC_REQUIRE(K <= 1024, "spmm: panel width above 1024");
-  const int chunk = cfg.chunk > 0 ? std::max(4, cfg.chunk / 4 * 4) : default_chunk(rows_in);
-  const int threads = cfg.threads == 128 ? 128 : 256;
+  const int dc = default_chunk(rows_in);
+  const int chunk = cfg.chunk > 0 ? std::min(dc, std::max(4, cfg.chunk / 4 * 4)) : dc;
+  const int threads = cfg.threads == 256 ? 256 : 128;
   const int64_t wpb = threads / 32;
   const int64_t blocks = (plan.nseg + wpb - 1) / wpb;
+  // the lane-group count follows the panel width and the default chunk, not
+  // the chunk in use, so every chunking sums each column's entries in the
+  // same order
+  const int G = spmm_groups(K, rows_in);
+  const int u = cfg.u > 0 ? cfg.u : 1;
   for (int c0 = 0; c0 < K; c0 += chunk) {
     const int kc = std::min(chunk, K - c0);
     const int K4 = kc / 4;
-    const int G = lane_groups(K4);
-    const int u = cfg.u > 0 ? cfg.u : default_u(G);
+    MC_REQUIRE(K4 <= 32 / G, "spmm: chunk wider than the lane groups");
 #define MC_SEG_ARGS u, blocks, threads, st, plan.nseg, plan.seg.as<int4>(), idx, val, X + c0, ld_x, K4, out + c0, ld_out, partial
     if (G == 16) launch_seg<16>(MC_SEG_ARGS);
     else if (G == 8) launch_seg<8>(MC_SEG_ARGS);

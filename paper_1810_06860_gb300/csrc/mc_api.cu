@@ -267,8 +267,25 @@ int ilog2(int64_t x) {
   return l;
 }
 
+// MC_SPMM_FORCE="u,threads,chunk" fixes the launch shape (tests compare
+// shapes bit for bit; 0 fields keep their defaults).
+const SpmmCfg *forced_cfg() {
+  static const SpmmCfg cfg = [] {
+    SpmmCfg c;
+    c.u = -1;
+    const char *v = std::getenv("MC_SPMM_FORCE");
+    if (v) {
+      int a = 0, b = 0, d = 0;
+      if (std::sscanf(v, "%d,%d,%d", &a, &b, &d) == 3) c = SpmmCfg{a, b, d};
+    }
+    return c;
+  }();
+  return cfg.u >= 0 ? &cfg : nullptr;
+}
+
 template <class F>
 SpmmCfg tuned_cfg(mc_handle h, int trans, int K, int64_t rows, int64_t rows_in, F &&launch) {
+  if (const SpmmCfg *f = forced_cfg()) return *f;
   if (!tune_enabled()) return SpmmCfg{};
   const TuneKey key{trans, K, ilog2(rows), ilog2(rows_in), ilog2(std::max<int64_t>(h->nnz, 1))};
   {
@@ -440,6 +457,22 @@ void draw_omega(mc_handle h, int kb, int kbp, uint64_t seed, uint64_t call_id, c
 // With the mixed-precision form the three panels that feed the Krylov
 // products (Omega, A^T Q_{i-1} and Q_{i-1}) are read as bf16; sums stay
 // float32 and the basis is orthonormalised in float32.
+// The whole block step (norms, two projections against the first cols
+// columns of Qp, CholeskyQR x3) as one cooperative launch for narrow blocks;
+// false when it does not apply (the caller runs the separate kernels).
+// MC_ORTH_FUSED=0 turns it off.
+bool orth_block_fused(mc_handle h, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
+                      int ldo) {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_ORTH_FUSED");
+    return !(v && v[0] == '0');
+  }();
+  if (!on || K > 32) return false;
+  float *scr = fbuf(h, h->tn_part, orth_narrow_scratch_floats(R, K, cols));
+  Scope sc(h, MC_T_GEMM, 4.0 * R * (2.0 * K + cols), 2.0 * R * K * (2.0 * cols + 1.5 * K));
+  return orth_narrow(h->stream, R, K, X, ldx, Qp, ldq, cols, out, ldo, nullptr, cols > 0, 1e-6f, 1e-10f, scr);
+}
+
 void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, const float *warm, int warm_ld,
                 int warm_cols) {
   const bool mixed = h->precision != 0;
@@ -451,7 +484,7 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
   float *T = fbuf(h, h->T, (size_t)h->n * kbp);
   if (mixed) spmm_Y_bf(h, bf_panel(h, h->Om_bf, h->n, kbp, h->Om.as<float>(), kbp), kbp, H, kbp);
   else spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // H_0 = A Omega
-  orth_block(h, h->m, kbp, H, kbp, Q, ktp);
+  if (!orth_block_fused(h, h->m, kbp, H, kbp, nullptr, 0, 0, Q, ktp)) orth_block(h, h->m, kbp, H, kbp, Q, ktp);
   for (int i = 1; i <= p; ++i) {
     if (mixed) {
       spmm_Yt_bf(h, bf_panel(h, h->Q_bf, h->m, kbp, Q + (size_t)(i - 1) * kbp, ktp), kbp, T, kbp);
@@ -460,6 +493,7 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
       spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, T, kbp);  // A^T Q_{i-1}
       spmm_Y(h, T, kbp, kbp, H, kbp);                          // A (A^T Q_{i-1})
     }
+    if (orth_block_fused(h, h->m, kbp, H, kbp, Q, ktp, i * kbp, Q + (size_t)i * kbp, ktp)) continue;
     float *ref = fbuf(h, h->lam, (size_t)kbp + colsumsq_scratch_floats(kbp));
     colsumsq(h->stream, h->m, kbp, H, kbp, ref, ref + kbp);
     project_out(h, h->m, Q, ktp, i * kbp, H, kbp, kbp);
@@ -797,6 +831,7 @@ mc_status svt_step(mc_handle h, mc_iter_info *out) {
   sync(h);
   const double err = std::sqrt(ssq) / h->normF;
   h->last_err = err;
+  if (!std::isfinite(err)) fail(MC_EINTERNAL, "non-finite residual on Phi at iteration " + std::to_string(it));
   const bool conv = err < P.eps;
   if (!conv) {
     if (err > h->prev_err) {

@@ -108,8 +108,9 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
 // plan.nslot * K floats.
 // rows_in: rows of X (sizes the column chunks so the panel slice stays in L2).
 // Launch shape of the SpMM: gathers in flight per lane group (u), CTA size
-// (threads: 128 or 256) and column-chunk width; 0 selects the default.  None
-// of them changes the order of any sum, so every choice gives the same bits.
+// (threads: 128 or 256) and column-chunk width; 0 selects the default.  The
+// lane-group count depends on the panel width only, so no choice changes the
+// order of any sum: every shape gives the same bits.
 struct SpmmCfg {
   int u = 0, threads = 0, chunk = 0;
 };
@@ -173,6 +174,15 @@ void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *
 // Gram on the tensor cores (k_tc.cu): G = X^T X for K <= 256, ld % 4 == 0,
 // X 16-byte aligned.  partial: gram_tc_scratch_floats(R, K) floats.  err
 // (device int, may be NULL) receives a nonzero code if a bounded wait expired.
+// One cooperative launch for a narrow Krylov block (K <= 32): column norms
+// (use_ref), two projections against Qp (R x cols), three CholeskyQR passes
+// (first shifted by shift_rel * trace / K and with the dependence test
+// G_jj <= ref_tol * norm_j^2), result into out.  Returns false (nothing
+// launched) when the rows do not fit the CTAs' shared memory or the device
+// has no cooperative launch; the caller then takes the separate kernels.
+size_t orth_narrow_scratch_floats(int64_t R, int K, int cols);
+bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
+                 int ldo, const float *ref_unused, bool use_ref, float shift_rel, float ref_tol, float *scratch);
 size_t gram_tc_scratch_floats(int64_t R, int K);
 bool gram_tc_supported(int K, int ld, const void *X);
 void gram_tc(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *G, int ld_g, float *partial, int *err);

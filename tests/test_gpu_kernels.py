@@ -148,3 +148,67 @@ def test_gram_tensor_cores(mc, R, K):
     # three TF32 products: about float32 accuracy relative to the entries' scale
     scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
     assert np.max(np.abs(G - ref) / scale) < 2e-5
+
+
+def test_eig_rank_deficient_krylov_gram(mc):
+    """Gram of a Krylov basis whose later blocks lost their leading columns
+    (they repeat a converged invariant subspace): 90 of 176 rows are exactly
+    zero and the trailing block of the reduction is pure rounding residue.
+    Reflecting that residue divides by a denormal; the solver must skip it."""
+    rng = np.random.default_rng(31)
+    K, kw, n = 176, 31, 2658
+    live = np.ones(K, bool)
+    for b in range(1, 4):
+        live[b * 44: b * 44 + 30] = False
+    nl = int(live.sum())
+    s = np.concatenate([27300 - 40 * np.arange(30), 5200 - 10 * np.arange(nl - 30)])
+    U, _ = np.linalg.qr(rng.standard_normal((n, nl)))
+    Vq, _ = np.linalg.qr(rng.standard_normal((nl, nl)))
+    B = np.zeros((n, K))
+    B[:, live] = (U * s) @ Vq.T
+    B = B.astype(np.float32).astype(np.float64)
+    G = (B.T @ B).astype(np.float32)
+    lam, W = mc.eig_sym(G, kw)
+    G64 = G.astype(np.float64)
+    ref = np.linalg.eigvalsh(G64)[::-1][:kw]
+    assert np.all(np.isfinite(lam)) and np.all(np.isfinite(W))
+    assert np.max(np.abs(np.sqrt(lam) - np.sqrt(ref))) <= 1e-5 * np.sqrt(ref[0])
+    W64 = W.astype(np.float64)
+    assert np.max(np.abs(W64.T @ W64 - np.eye(kw))) < 1e-4
+    assert np.max(np.linalg.norm(G64 @ W64 - W64 * lam.astype(np.float64), axis=0)) <= 1e-4 * ref[0]
+
+
+_SHAPE_PROBE = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import mc_synth, paper_1810_06860_gb300 as mc
+o = mc_synth.ratings(m=4000, n=1500, N=150000, seed=2)
+rng = np.random.default_rng(0)
+out = []
+with mc.Handle.from_observed(o) as h:
+    for K in (4, 12, 60, 200):
+        out.append(h.spmm(rng.standard_normal((o.n, K)).astype(np.float32)))
+        out.append(h.spmm(rng.standard_normal((o.m, K)).astype(np.float32), trans=True))
+np.savez({path!r}, *out)
+"""
+
+
+def test_spmm_launch_shapes_bit_identical(mc, tmp_path):
+    """Every SpMM launch shape the autotuner may pick (gathers in flight, CTA
+    size, column chunk) gives the same bits."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = []
+    for force in ("1,128,128", "4,256,32", "2,256,64", "1,128,16"):
+        path = str(tmp_path / f"s{len(res)}.npz")
+        env = dict(os.environ, MC_SPMM_FORCE=force)
+        subprocess.run([sys.executable, "-c", _SHAPE_PROBE.format(root=root, path=path)], env=env, check=True,
+                       timeout=600)
+        z = np.load(path)
+        res.append([z[f"arr_{i}"] for i in range(len(z.files))])
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert np.array_equal(a, b)
