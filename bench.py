@@ -45,7 +45,7 @@ K_BKI, S_OVER, P_BKI = 50, 10, 3
 HBM_FALLBACK_GBS = 6800.0
 # Serving: a bounded sample of the Poisson job stream (m, n log-uniform in
 # [256, 8192], 5-50% observed, rank 5-50), submitted at its arrival times.
-SERVE_JOBS, SERVE_RATE, SERVE_SLOTS, SERVE_IMAX = 48, 16.0, 16, 300
+SERVE_JOBS, SERVE_RATE, SERVE_SLOTS, SERVE_IMAX = 32, 16.0, 8, 300
 
 
 def workload_config():

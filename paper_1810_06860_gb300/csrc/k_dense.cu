@@ -675,32 +675,84 @@ __device__ __forceinline__ void on_reduce(const OrthNarrowArgs &a, int count, in
   }
 }
 
-__global__ void __launch_bounds__(ON_THREADS, 1) orth_narrow_kernel(OrthNarrowArgs a) {
+// Row strides of the shared-memory copies: multiples of 4 floats (16-byte
+// rows) with an odd number of 16-byte groups, so eight consecutive rows read
+// with 16-byte loads fall in distinct bank groups.
+__host__ __device__ inline int on_ld(int w) {
+  const int w4 = (w + 3) / 4 * 4;
+  return ((w4 / 4) & 1) ? w4 : w4 + 4;
+}
+
+// partial[ti][tj] (4 x 4 tiles) of A^T B over the CTA's rows, A = As (width
+// na, stride lda), B = Bs (width nb4*4, stride ldb); tiles with ti > tj are
+// skipped when upper.  Groups of threads take interleaved rows; their tile
+// sums meet in shared memory in group order.  Writes count = na4*4 x nb4*4
+// values (row-major, width nb4*4) to dst.
+__device__ __forceinline__ void on_tile_products(const float *As, int lda, int na4, const float *Bs, int ldb, int nb4,
+                                                 int nr, bool upper, float *red, float *dst) {
+  const int tid = threadIdx.x;
+  const int T = na4 * nb4;
+  const int G = max(1, ON_THREADS / T);
+  float acc[4][4] = {};
+  const int tile = tid % T, g = tid / T;
+  const int ti = tile / nb4, tj = tile % nb4;
+  const bool act = g < G && tid < T * G && !(upper && ti > tj);
+  if (act)
+    for (int r = g; r < nr; r += G) {
+      const float4 x = *reinterpret_cast<const float4 *>(As + r * lda + 4 * ti);
+      const float4 y = *reinterpret_cast<const float4 *>(Bs + r * ldb + 4 * tj);
+      const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xv[u], yv[v], acc[u][v]);
+    }
+  if (tid < T * G)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) red[(size_t)tid * 16 + u * 4 + v] = act ? acc[u][v] : 0.f;
+  __syncthreads();
+  const int W = nb4 * 4;
+  for (int o = tid; o < T * 16; o += ON_THREADS) {
+    const int t = o / 16, e = o % 16;
+    float sum = 0.f;
+    for (int q = 0; q < G; ++q) sum += red[(size_t)(q * T + t) * 16 + e];
+    const int i = (t / nb4) * 4 + e / 4, j = (t % nb4) * 4 + e % 4;
+    dst[i * W + j] = sum;
+  }
+  __syncthreads();
+}
+
+template <int KM>
+__global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kernel(OrthNarrowArgs a) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) float onsm[];
   const int K = a.K, cols = a.cols, tid = threadIdx.x;
-  const int ldh = K + 1;           // row padding against bank conflicts
+  const int K4 = (K + 3) / 4, C4 = (cols + 3) / 4, KW = K4 * 4, CW = C4 * 4;
+  const int ldh = on_ld(K), ldq = on_ld(cols);
   const int64_t r0 = blockIdx.x * a.rows_per;
   const int64_t r1 = a.R < r0 + a.rows_per ? a.R : r0 + a.rows_per;
   const int nr = r1 > r0 ? static_cast<int>(r1 - r0) : 0;
-  float *Hs = onsm;                                   // nr x ldh
-  float *Qs = Hs + (size_t)a.rows_per * ldh;          // nr x cols
-  float *Ms = Qs + (size_t)a.rows_per * cols;         // cols x K (C) or K x K (G)
-  float *Ls = Ms + (size_t)max(cols, K) * K;          // K x (K+1): Cholesky factor
+  float *Hs = onsm;                                   // rows_per x ldh (zero beyond K)
+  float *Qs = Hs + (size_t)a.rows_per * ldh;          // rows_per x ldq (zero beyond cols)
+  float *Ms = Qs + (size_t)a.rows_per * ldq;          // CW x KW (C) or KW x KW (G), and the partial tile
+  float *red = Ms + (size_t)max(CW, KW) * KW;         // ON_THREADS x 16
+  float *Ls = red + (size_t)ON_THREADS * 16;          // K x (K+1): Cholesky factor
   float *Bs = Ls + (size_t)K * (K + 1);               // K x (K+1): running inverse
   float *fl = Bs + (size_t)K * (K + 1);               // K flags
   float *refs = fl + K;                               // K column norms^2
-  const int stride = max(cols * K + K, K * K);
-  float *fin_C = a.fin, *fin_G = a.fin + cols * K + K;
+  const int stride = max(CW * KW + KW, KW * KW);  // per-CTA partials of C (+ norms) or of G
+  float *fin_C = a.fin, *fin_G = a.fin + stride;
 
-  for (int t = tid; t < nr * K; t += ON_THREADS) {
-    const int r = t / K, c = t % K;
-    Hs[r * ldh + c] = a.X[(r0 + r) * a.ldx + c];
+  for (int t = tid; t < nr * ldh; t += ON_THREADS) {
+    const int r = t / ldh, c = t % ldh;
+    Hs[t] = c < K ? a.X[(r0 + r) * a.ldx + c] : 0.f;
   }
-  for (int t = tid; t < nr * cols; t += ON_THREADS) {
-    const int r = t / cols, c = t % cols;
-    Qs[r * cols + c] = a.Qp[(r0 + r) * a.ldq + c];
+  for (int t = tid; t < nr * ldq; t += ON_THREADS) {
+    const int r = t / ldq, c = t % ldq;
+    Qs[t] = c < cols ? a.Qp[(r0 + r) * a.ldq + c] : 0.f;
   }
   __syncthreads();
 
@@ -708,66 +760,77 @@ __global__ void __launch_bounds__(ON_THREADS, 1) orth_narrow_kernel(OrthNarrowAr
   // dependence test of the first pass) ride along with the first product
   const int nref = a.use_ref ? K : 0;
   for (int rep = 0; rep < 2 && cols > 0; ++rep) {
-    const int cnt = cols * K + (rep == 0 ? nref : 0);
-    for (int o = tid; o < cnt; o += ON_THREADS) {
-      float acc = 0.f;
-      if (o < cols * K) {
-        const int i = o / K, j = o % K;
-        for (int r = 0; r < nr; ++r) acc = fmaf(Qs[r * cols + i], Hs[r * ldh + j], acc);
-      } else {
-        const int c = o - cols * K;
-        for (int r = 0; r < nr; ++r) acc = fmaf(Hs[r * ldh + c], Hs[r * ldh + c], acc);
-      }
-      a.part[(int64_t)blockIdx.x * stride + o] = acc;
-    }
-    grid.sync();
-    on_reduce(a, cnt, stride, fin_C);
-    grid.sync();
-    for (int o = tid; o < cols * K; o += ON_THREADS) Ms[o] = fin_C[o];
+    float *dst = a.part + (int64_t)blockIdx.x * stride;
+    on_tile_products(Qs, ldq, C4, Hs, ldh, K4, nr, false, red, dst);
     if (rep == 0)
-      for (int c = tid; c < nref; c += ON_THREADS) refs[c] = fin_C[cols * K + c];
+      for (int c = tid; c < nref; c += ON_THREADS) {
+        float acc = 0.f;
+        for (int r = 0; r < nr; ++r) acc = fmaf(Hs[r * ldh + c], Hs[r * ldh + c], acc);
+        dst[CW * KW + c] = acc;
+      }
+    grid.sync();
+    on_reduce(a, CW * KW + (rep == 0 ? nref : 0), stride, fin_C);
+    grid.sync();
+    for (int o = tid; o < CW * KW; o += ON_THREADS) Ms[o] = fin_C[o];
+    if (rep == 0)
+      for (int c = tid; c < nref; c += ON_THREADS) refs[c] = fin_C[CW * KW + c];
     __syncthreads();
-    for (int t = tid; t < nr * K; t += ON_THREADS) {
-      const int r = t / K, j = t % K;
-      float acc = 0.f;
-      for (int i = 0; i < cols; ++i) acc = fmaf(Qs[r * cols + i], Ms[i * K + j], acc);
-      Hs[r * ldh + j] -= acc;
+    // a thread per row: out = h - q C with q (the row of Qp) read 4 at a time
+    for (int r = tid; r < nr; r += ON_THREADS) {
+      float out[KM];
+#pragma unroll
+      for (int j = 0; j < KM; ++j) out[j] = j < K ? Hs[r * ldh + j] : 0.f;
+      for (int i4 = 0; i4 < C4; ++i4) {
+        const float4 q4 = *reinterpret_cast<const float4 *>(Qs + r * ldq + 4 * i4);
+        const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float *crow = Ms + (4 * i4 + u) * KW;
+#pragma unroll
+          for (int j4 = 0; j4 < KM / 4; ++j4) {
+            if (j4 < K4) {
+              const float4 c4 = *reinterpret_cast<const float4 *>(crow + 4 * j4);
+              out[4 * j4 + 0] = fmaf(-qv[u], c4.x, out[4 * j4 + 0]);
+              out[4 * j4 + 1] = fmaf(-qv[u], c4.y, out[4 * j4 + 1]);
+              out[4 * j4 + 2] = fmaf(-qv[u], c4.z, out[4 * j4 + 2]);
+              out[4 * j4 + 3] = fmaf(-qv[u], c4.w, out[4 * j4 + 3]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (j < K) Hs[r * ldh + j] = out[j];
     }
     __syncthreads();
   }
 
   // three CholeskyQR passes: X <- X R^{-1} with X^T X + shift I = R^T R
   for (int pass = 0; pass < 3; ++pass) {
-    for (int o = tid; o < K * K; o += ON_THREADS) {
-      const int i = o / K, j = o % K;
-      float acc = 0.f;
-      if (i <= j)
-        for (int r = 0; r < nr; ++r) acc = fmaf(Hs[r * ldh + i], Hs[r * ldh + j], acc);
-      a.part[(int64_t)blockIdx.x * stride + o] = acc;
-    }
+    on_tile_products(Hs, ldh, K4, Hs, ldh, K4, nr, true, red, a.part + (int64_t)blockIdx.x * stride);
     grid.sync();
-    on_reduce(a, K * K, stride, fin_G);
+    on_reduce(a, KW * KW, stride, fin_G);
     grid.sync();
     // G (upper triangle reduced; mirrored) -> L L^T and L^{-1}, as chol_inv
     __shared__ float s_tr, s_max;
     if (tid == 0) {
       float tr = 0.f, mx = 0.f;
       for (int i = 0; i < K; ++i) {
-        tr += fin_G[i * K + i];
-        mx = fmaxf(mx, fin_G[i * K + i]);
+        tr += fin_G[i * KW + i];
+        mx = fmaxf(mx, fin_G[i * KW + i]);
       }
       s_tr = tr;
       s_max = mx;
     }
     for (int i = tid; i < K; i += ON_THREADS)
-      fl[i] = (pass == 0 && a.use_ref && !(fin_G[i * K + i] > a.ref_tol * refs[i])) ? 0.f : 1.f;
+      fl[i] = (pass == 0 && a.use_ref && !(fin_G[i * KW + i] > a.ref_tol * refs[i])) ? 0.f : 1.f;
     __syncthreads();
     const float shift = (pass == 0 ? a.shift_rel : 0.f) * s_tr / K;
     const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
     for (int t = tid; t < K * K; t += ON_THREADS) {
       const int i = t / K, j = t % K;
       const bool live = fl[i] != 0.f && fl[j] != 0.f;
-      Ls[i * (K + 1) + j] = (j <= i && live) ? fin_G[j * K + i] + (i == j ? shift : 0.f) : 0.f;
+      Ls[i * (K + 1) + j] = (j <= i && live) ? fin_G[j * KW + i] + (i == j ? shift : 0.f) : 0.f;
       Bs[i * (K + 1) + j] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
@@ -792,11 +855,11 @@ __global__ void __launch_bounds__(ON_THREADS, 1) orth_narrow_kernel(OrthNarrowAr
     }
     // X <- X R^{-1}, R^{-1}[l][c] = L^{-1}[c][l] (kept l, c only), a thread per row
     for (int r = tid; r < nr; r += ON_THREADS) {
-      float h[ON_MAXK];
+      float h[KM];
 #pragma unroll
-      for (int l = 0; l < ON_MAXK; ++l) h[l] = (l < K && fl[l] != 0.f) ? Hs[r * ldh + l] : 0.f;
+      for (int l = 0; l < KM; ++l) h[l] = (l < K && fl[l] != 0.f) ? Hs[r * ldh + l] : 0.f;
 #pragma unroll
-      for (int c = 0; c < ON_MAXK; ++c) {
+      for (int c = 0; c < KM; ++c) {
         if (c < K) {
           float acc = 0.f;
           if (fl[c] != 0.f) {
@@ -953,7 +1016,10 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
   MC_CHECK_LAUNCH();
 }
 
-static int64_t on_stride(int K, int cols) { return std::max<int64_t>((int64_t)cols * K + K, (int64_t)K * K); }
+static int64_t on_stride(int K, int cols) {
+  const int64_t KW = (K + 3) / 4 * 4, CW = (cols + 3) / 4 * 4;
+  return std::max(CW * KW + KW, KW * KW);
+}
 
 size_t orth_narrow_scratch_floats(int64_t R, int K, int cols) {
   (void)R;
@@ -961,33 +1027,40 @@ size_t orth_narrow_scratch_floats(int64_t R, int K, int cols) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   const int64_t nb_max = (int64_t)std::max(sms, 1) * 4;
-  return (size_t)(nb_max * on_stride(K, cols) + (int64_t)cols * K + K + (int64_t)K * K + 64);
+  const int64_t st = on_stride(K, cols);
+  return (size_t)(nb_max * st + 2 * st + 64);
 }
 
 static size_t on_smem(int64_t rows_per, int K, int cols) {
-  return sizeof(float) * ((size_t)rows_per * (K + 1) + (size_t)rows_per * cols + (size_t)std::max(cols, K) * K +
-                          2 * (size_t)K * (K + 1) + 2 * (size_t)K);
+  const int KW = (K + 3) / 4 * 4, CW = (cols + 3) / 4 * 4;
+  return sizeof(float) * ((size_t)rows_per * on_ld(K) + (size_t)rows_per * on_ld(cols) +
+                          (size_t)std::max(CW, KW) * KW + (size_t)ON_THREADS * 16 + 2 * (size_t)K * (K + 1) +
+                          2 * (size_t)K);
 }
 
 bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
                  int ldo, const float *ref_unused, bool use_ref, float shift_rel, float ref_tol, float *scratch) {
   (void)ref_unused;
   if (K < 1 || K > ON_MAXK || R < 1 || cols < 0) return false;
+  if (((cols + 3) / 4) * ((K + 3) / 4) > ON_THREADS) return false;  // one 4 x 4 tile of Qp^T X per thread at most
   int dev = 0, sms = 0, coop = 0;
   MC_CUDA(cudaGetDevice(&dev));
   MC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   MC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop || sms <= 0) return false;
-  MC_CUDA(cudaFuncSetAttribute(orth_narrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  const bool small = K <= 16;
+  const void *fn = small ? reinterpret_cast<const void *>(orth_narrow_kernel<16>)
+                         : reinterpret_cast<const void *>(orth_narrow_kernel<32>);
+  MC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   // CTAs: one to four per SM, at least 32 rows each, the rows and the
   // panel slices of a CTA in at most 220 KB / CTAs-per-SM of shared memory
-  for (int per_sm = 1; per_sm <= 4; ++per_sm) {
+  for (int per_sm = 4; per_sm >= 1; --per_sm) {
     const int64_t nb = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (R + 31) / 32));
     const int64_t rows_per = (R + nb - 1) / nb;
     const size_t smem = on_smem(rows_per, K, cols);
     if (smem > (size_t)220 * 1024 / per_sm) continue;
     int occ = 0;
-    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, orth_narrow_kernel, ON_THREADS, smem));
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, ON_THREADS, smem));
     if ((int64_t)occ * sms < nb) continue;
     const int64_t stride = on_stride(K, cols);
     OrthNarrowArgs a{};
@@ -1007,8 +1080,7 @@ bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const flo
     a.shift_rel = shift_rel;
     a.ref_tol = ref_tol;
     void *args[] = {&a};
-    MC_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(orth_narrow_kernel), dim3((unsigned)nb),
-                                        dim3(ON_THREADS), args, smem, st));
+    MC_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)nb), dim3(ON_THREADS), args, smem, st));
     count_launch();
     return true;
   }

@@ -37,6 +37,8 @@ constexpr int EIG_THREADS = 1024;
 constexpr int NW = EIG_THREADS / 32;
 constexpr size_t EIG_SMEM = 220 * 1024;
 constexpr int HV_CHUNK = 16;       // reflectors staged per back-transformation chunk
+constexpr int ST_BISECT = 1, ST_INVIT = 2, ST_GS = 4, ST_BACK = 8, ST_ALL = 15;
+constexpr int SPLIT_K = 256;       // above: inverse iteration and back-transformation on many CTAs
 
 __device__ __forceinline__ int pk(int r, int c) { return r * (r + 1) / 2 + c; }  // r >= c
 
@@ -353,7 +355,7 @@ struct VecLayout {
 __global__ void __launch_bounds__(EIG_THREADS, 1)
 eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__restrict__ g_e,
                    const float *__restrict__ g_beta, const float *__restrict__ Hv, float *__restrict__ lam_out,
-                   float *__restrict__ W, int ld_w, float *__restrict__ gw, VecLayout lay) {
+                   float *__restrict__ W, int ld_w, float *__restrict__ gw, VecLayout lay, int stages) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float red[2][32];
   __shared__ float s_glo, s_ghi, s_pivmin;
@@ -381,6 +383,7 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
   }
   __syncthreads();
 
+  if (stages & ST_BISECT) {
   // ---- multisection ----
   if (tid < 32) {
     float glo = FLT_MAX, ghi = -FLT_MAX, emax = 0.f;
@@ -454,6 +457,13 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
   for (int t = tid; t < kw; t += EIG_THREADS) lam[t] = 0.5f * (lo[t] + hi[t]);
   __syncthreads();
 
+  for (int t = tid; t < kw; t += EIG_THREADS) lam_out[t] = lam[t];
+  }  // ST_BISECT
+  if (stages & ST_INVIT) {
+  if (!(stages & ST_BISECT)) {
+    for (int t = tid; t < kw; t += EIG_THREADS) lam[t] = lam_out[t];
+    __syncthreads();
+  }
   // ---- inverse iteration, B eigenvalues at a time ----
   const float tnorm = fmaxf(fabsf(s_glo), fabsf(s_ghi));
   const float tol_c = 1e-5f * tnorm;
@@ -543,6 +553,8 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
     __syncthreads();
   }
 
+  }  // ST_INVIT
+  if (stages & ST_GS) {
   // ---- Gram-Schmidt twice ----
   int rb = 0;
   for (int j = 0; j < kw; ++j) {
@@ -579,6 +591,8 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
     }
   }
 
+  }  // ST_GS
+  if (!(stages & ST_BACK)) return;
   // ---- back-transformation: Z <- H_0 H_1 ... H_{K-3} Z ----
   for (int top = K - 3; top >= 0; top -= HV_CHUNK) {
     const int lowi = max(0, top - HV_CHUNK + 1);
@@ -614,11 +628,147 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
     }
   }
 
-  for (int t = tid; t < kw; t += EIG_THREADS) lam_out[t] = lam[t];
   for (int64_t f = tid; f < (int64_t)K * kw; f += EIG_THREADS) {
     const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
     W[(int64_t)a * ld_w + t] = Z[(int64_t)a * ldz + t];
   }
+}
+
+// ---- wide matrices: the per-eigenvalue stages on many CTAs ------------------
+// Inverse iteration for eigenvalue blockIdx.x (one thread; the LU factors and
+// the vector in the CTA's shared memory), the same steps as in
+// eig_vectors_kernel; the vector goes to Z (global, row stride ldz).
+__global__ void __launch_bounds__(32)
+eig_invit_kernel(int K, int kw, const float *__restrict__ g_d, const float *__restrict__ g_e,
+                 const float *__restrict__ lam_g, float *__restrict__ Z, int ldz) {
+  extern __shared__ __align__(16) float ism[];
+  float *d = ism, *e = d + K, *fa = e + K, *fb = fa + K, *fc = fb + K, *fl = fc + K, *z = fl + K;
+  const int lane = threadIdx.x, t = blockIdx.x;
+  float glo = FLT_MAX, ghi = -FLT_MAX;
+  for (int a = lane; a < K; a += 32) {
+    d[a] = g_d[a];
+    e[a] = g_e[a];
+  }
+  __syncwarp();
+  for (int a = lane; a < K; a += 32) {
+    const float r = (a > 0 ? fabsf(e[a - 1]) : 0.f) + (a + 1 < K ? fabsf(e[a]) : 0.f);
+    glo = fminf(glo, d[a] - r);
+    ghi = fmaxf(ghi, d[a] + r);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    glo = fminf(glo, __shfl_xor_sync(0xffffffffu, glo, off));
+    ghi = fmaxf(ghi, __shfl_xor_sync(0xffffffffu, ghi, off));
+  }
+  const float span = fmaxf(ghi - glo, fmaxf(fabsf(glo), fabsf(ghi)) * 1e-6f) + 1e-30f;
+  const float s_glo = glo - 1e-3f * span, s_ghi = ghi + 1e-3f * span;
+  if (lane != 0) return;
+  const float tnorm = fmaxf(fabsf(s_glo), fabsf(s_ghi));
+  const float tol_c = 1e-5f * tnorm;
+  const float lt = lam_g[t];
+  const bool clus = (t > 0 && lam_g[t - 1] - lt <= tol_c) || (t + 1 < kw && lt - lam_g[t + 1] <= tol_c);
+  const float lm = lt + (clus ? 2.0f * tol_c * (1.0f + 0.01f * (float)(t % 64)) : 0.f);
+  const float tiny = fmaxf(FLT_EPSILON * tnorm, FLT_MIN);
+  unsigned piv_bits[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) piv_bits[q] = 0u;
+  float a_cur = d[0] - lm, b_cur = K > 1 ? e[0] : 0.f;
+  for (int a = 0; a + 1 < K; ++a) {
+    const float cc = e[a];
+    const float a_next = d[a + 1] - lm;
+    const float b_next = a + 2 < K ? e[a + 1] : 0.f;
+    float l, du2 = 0.f, na, nb;
+    if (fabsf(a_cur) >= fabsf(cc)) {
+      if (a_cur == 0.f) a_cur = tiny;
+      l = cc / a_cur;
+      na = a_next - l * b_cur;
+      nb = b_next;
+    } else {
+      l = a_cur / cc;
+      na = b_cur - l * a_next;
+      du2 = b_next;
+      nb = -l * b_next;
+      a_cur = cc;
+      b_cur = a_next;
+      piv_bits[a >> 5] |= 1u << (a & 31);
+    }
+    fa[a] = 1.0f / (fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
+    fb[a] = b_cur;
+    fc[a] = du2;
+    fl[a] = l;
+    a_cur = na;
+    b_cur = nb;
+  }
+  fa[K - 1] = 1.0f / (fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
+  fb[K - 1] = 0.f;
+  fc[K - 1] = 0.f;
+  for (int a = 0; a < K; ++a)
+    z[a] = (float)(hash32((uint32_t)(a * 7919 + t * 104729 + 12345)) >> 8) * (1.0f / 16777216.0f) - 0.5f;
+  for (int rep = 0; rep < 3; ++rep) {
+    float ya = z[0];
+    for (int a = 0; a + 1 < K; ++a) {
+      float yb = z[a + 1];
+      if (piv_bits[a >> 5] & (1u << (a & 31))) {
+        const float tmp = ya;
+        ya = yb;
+        yb = tmp - fl[a] * ya;
+      } else {
+        yb -= fl[a] * ya;
+      }
+      z[a] = ya;
+      ya = yb;
+    }
+    float x1 = ya * fa[K - 1], x2 = 0.f;
+    z[K - 1] = x1;
+    float nrm = fabsf(x1);
+    for (int a = K - 2; a >= 0; --a) {
+      const float xx = (z[a] - fb[a] * x1 - fc[a] * x2) * fa[a];
+      z[a] = xx;
+      x2 = x1;
+      x1 = xx;
+      nrm = fmaxf(nrm, fabsf(xx));
+    }
+    const bool fin = nrm <= FLT_MAX;
+    const float sc = fin ? (nrm > 0.f ? 1.0f / nrm : 1.0f) : 0.f;
+    for (int a = 0; a < K; ++a)
+      z[a] = fin ? z[a] * sc
+                 : (float)(hash32((uint32_t)(a * 7919 + t * 104729 + 12345)) >> 8) * (1.0f / 16777216.0f) - 0.5f;
+  }
+  for (int a = 0; a < K; ++a) Z[(int64_t)a * ldz + t] = z[a];
+}
+
+// Back-transformation of vector blockIdx.x by the reflectors (the vector in
+// shared memory, each reflector read once from global memory), then W.
+constexpr int BT_THREADS = 256;
+__global__ void __launch_bounds__(BT_THREADS)
+eig_backtr_kernel(int K, const float *__restrict__ g_beta, const float *__restrict__ Hv,
+                  const float *__restrict__ Z, int ldz, float *__restrict__ W, int ld_w) {
+  extern __shared__ __align__(16) float bsm[];
+  __shared__ float red[2][BT_THREADS / 32];
+  float *z = bsm;
+  const int t = blockIdx.x, tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  for (int a = tid; a < K; a += BT_THREADS) z[a] = Z[(int64_t)a * ldz + t];
+  __syncthreads();
+  int rb = 0;
+  for (int i = K - 3; i >= 0; --i) {
+    const float bt = g_beta[i];
+    if (bt == 0.f) continue;
+    const int n = K - 1 - i;
+    const float *v = Hv + (int64_t)i * K;
+    float acc = 0.f;
+    for (int a = tid; a < n; a += BT_THREADS) acc = fmaf(v[a], z[i + 1 + a], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) red[rb][wid] = acc;
+    __syncthreads();
+    float sdot = 0.f;
+#pragma unroll
+    for (int q = 0; q < BT_THREADS / 32; ++q) sdot += red[rb][q];
+    rb ^= 1;
+    const float h = bt * sdot;
+    for (int a = tid; a < n; a += BT_THREADS) z[i + 1 + a] -= v[a] * h;
+    __syncthreads();
+  }
+  for (int a = tid; a < K; a += BT_THREADS) W[(int64_t)a * ld_w + t] = z[a];
 }
 
 // ------------------------------------------------------------------ plans --
@@ -669,9 +819,10 @@ EigPlan eig_plan(int K, int kw) {
   off += pl.coop ? 1024 : 0;
   VecLayout vl{};
   vl.ldz = kw | 1;
+  const bool split = K > SPLIT_K;
   const size_t vfixed = sizeof(float) * (3 * (size_t)K + 4 * (size_t)kw + NW * 32 + (size_t)HV_CHUNK * K) + 16;
   const size_t zbytes = sizeof(float) * (size_t)K * vl.ldz;
-  vl.z_in_smem = vfixed + zbytes <= EIG_SMEM;
+  vl.z_in_smem = !split && vfixed + zbytes <= EIG_SMEM;
   const size_t avail = EIG_SMEM - vfixed - (vl.z_in_smem ? zbytes : 0);
   int batch = static_cast<int>(std::min<size_t>(32, avail / (sizeof(float) * 4 * (size_t)K)));
   vl.f_in_smem = batch >= 8;
@@ -733,8 +884,27 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   }
 #undef MC_TRI_ARGS
   MC_CHECK_LAUNCH();
+  if (K <= SPLIT_K) {
+    eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                           gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_ALL);
+    MC_CHECK_LAUNCH();
+    return;
+  }
+  // wide: multisection (one CTA), inverse iteration (a CTA per eigenvalue),
+  // Gram-Schmidt (one CTA), back-transformation (a CTA per vector)
+  float *Zg = gw + pl.vl.g_z;
   eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
-                                                         gw + pl.g_hv, lam, W, ld_w, gw, pl.vl);
+                                                         gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_BISECT);
+  MC_CHECK_LAUNCH();
+  const size_t ism = sizeof(float) * 7 * (size_t)K;
+  MC_CUDA(cudaFuncSetAttribute(eig_invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(7 * 4 * 1024)));
+  eig_invit_kernel<<<kw, 32, ism, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam, Zg, pl.vl.ldz);
+  MC_CHECK_LAUNCH();
+  eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                         gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_GS);
+  MC_CHECK_LAUNCH();
+  eig_backtr_kernel<<<kw, BT_THREADS, sizeof(float) * (size_t)K, st>>>(K, gw + pl.g_beta, gw + pl.g_hv, Zg,
+                                                                       pl.vl.ldz, W, ld_w);
   MC_CHECK_LAUNCH();
 }
 
