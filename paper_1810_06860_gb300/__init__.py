@@ -40,7 +40,7 @@ def _is_torch(a) -> bool:
 
 
 def _ptr(a, dtype):
-    """(pointer, keepalive) for a host NumPy array or a CUDA torch tensor."""
+    """(pointer, keepalive) for a host NumPy array or a torch tensor (CUDA or host)."""
     if a is None:
         return None, None
     if _is_torch(a):

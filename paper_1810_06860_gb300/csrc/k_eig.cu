@@ -39,21 +39,9 @@ constexpr size_t EIG_SMEM = 220 * 1024;
 constexpr int HV_CHUNK = 16;       // reflectors staged per back-transformation chunk
 constexpr int ST_BISECT = 1, ST_INVIT = 2, ST_GS = 4, ST_BACK = 8, ST_ALL = 15;
 constexpr int SPLIT_K = 256;       // above: inverse iteration and back-transformation on many CTAs
+constexpr int SMALL_K = 128;       // up to here: 256-thread CTAs
 
 __device__ __forceinline__ int pk(int r, int c) { return r * (r + 1) / 2 + c; }  // r >= c
-
-// Block-wide sum returned to every thread (one barrier).  Successive calls
-// must alternate buffers.
-__device__ __forceinline__ float block_sum1(float v, float *red) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = 0.f;
-#pragma unroll 8
-  for (int q = 0; q < NW; ++q) t += red[q];
-  return t;
-}
 
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   x ^= x >> 16;
@@ -352,10 +340,12 @@ struct VecLayout {
   int64_t g_f;
 };
 
-__global__ void __launch_bounds__(EIG_THREADS, 1)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__restrict__ g_e,
                    const float *__restrict__ g_beta, const float *__restrict__ Hv, float *__restrict__ lam_out,
                    float *__restrict__ W, int ld_w, float *__restrict__ gw, VecLayout lay, int stages) {
+  constexpr int NWV = THREADS / 32;
   extern __shared__ __align__(16) float sm[];
   __shared__ float red[2][32];
   __shared__ float s_glo, s_ghi, s_pivmin;
@@ -369,14 +359,14 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
   float *hi = lo + kw;            // kw
   float *hvec = hi + kw;          // kw
   float *part = hvec + kw;        // NW x 32
-  float *hv = part + NW * 32;     // HV_CHUNK x K
+  float *hv = part + NWV * 32;     // HV_CHUNK x K
   float *big = hv + (size_t)HV_CHUNK * K;
   big = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(big) + 15) & ~uintptr_t(15));
   float *Z = lay.z_in_smem ? big : gw + lay.g_z;
   float *F = lay.f_in_smem ? (lay.z_in_smem ? big + (size_t)K * ldz : big) : gw + lay.g_f;
   const int B = lay.batch;
 
-  for (int a = tid; a < K; a += EIG_THREADS) {
+  for (int a = tid; a < K; a += THREADS) {
     d[a] = g_d[a];
     e[a] = g_e[a];
     beta[a] = g_beta[a];
@@ -406,15 +396,15 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
     }
   }
   __syncthreads();
-  for (int t = tid; t < kw; t += EIG_THREADS) {
+  for (int t = tid; t < kw; t += THREADS) {
     lo[t] = s_glo;
     hi[t] = s_ghi;
   }
   __syncthreads();
   {
     int g = 32;
-    while (g > 1 && kw * g > EIG_THREADS) g >>= 1;
-    const int groups = EIG_THREADS / g;
+    while (g > 1 && kw * g > THREADS) g >>= 1;
+    const int groups = THREADS / g;
     for (int t0 = 0; t0 < kw; t0 += groups) {
       const int t = t0 + tid / g, q = tid % g;
       const int target = K - 1 - t;
@@ -454,14 +444,14 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
       }
     }
   }
-  for (int t = tid; t < kw; t += EIG_THREADS) lam[t] = 0.5f * (lo[t] + hi[t]);
+  for (int t = tid; t < kw; t += THREADS) lam[t] = 0.5f * (lo[t] + hi[t]);
   __syncthreads();
 
-  for (int t = tid; t < kw; t += EIG_THREADS) lam_out[t] = lam[t];
+  for (int t = tid; t < kw; t += THREADS) lam_out[t] = lam[t];
   }  // ST_BISECT
   if (stages & ST_INVIT) {
   if (!(stages & ST_BISECT)) {
-    for (int t = tid; t < kw; t += EIG_THREADS) lam[t] = lam_out[t];
+    for (int t = tid; t < kw; t += THREADS) lam[t] = lam_out[t];
     __syncthreads();
   }
   // ---- inverse iteration, B eigenvalues at a time ----
@@ -565,28 +555,28 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
           const int l = c0 + lane;
           float acc = 0.f;
           if (l < j)
-            for (int a = wid; a < K; a += NW) acc = fmaf(Z[(int64_t)a * ldz + l], Z[(int64_t)a * ldz + j], acc);
+            for (int a = wid; a < K; a += NWV) acc = fmaf(Z[(int64_t)a * ldz + l], Z[(int64_t)a * ldz + j], acc);
           part[wid * 32 + lane] = acc;
           __syncthreads();
           if (tid < 32 && c0 + tid < j) {
             float s = 0.f;
-            for (int w = 0; w < NW; ++w) s += part[w * 32 + tid];
+            for (int w = 0; w < NWV; ++w) s += part[w * 32 + tid];
             hvec[c0 + tid] = s;
           }
           __syncthreads();
         }
       }
       float nrm_part = 0.f;
-      for (int a = tid; a < K; a += EIG_THREADS) {
+      for (int a = tid; a < K; a += THREADS) {
         float z = Z[(int64_t)a * ldz + j];
         for (int l = 0; l < j; ++l) z = fmaf(-Z[(int64_t)a * ldz + l], hvec[l], z);
         Z[(int64_t)a * ldz + j] = z;
         nrm_part = fmaf(z, z, nrm_part);
       }
-      const float nrm2 = block_sum1(nrm_part, red[rb]);
+      const float nrm2 = block_sum_n<NWV>(nrm_part, red[rb]);
       rb ^= 1;
       const float sc = nrm2 > 0.f ? rsqrtf(nrm2) : 0.f;
-      for (int a = tid; a < K; a += EIG_THREADS) Z[(int64_t)a * ldz + j] *= sc;
+      for (int a = tid; a < K; a += THREADS) Z[(int64_t)a * ldz + j] *= sc;
       __syncthreads();
     }
   }
@@ -596,7 +586,7 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
   // ---- back-transformation: Z <- H_0 H_1 ... H_{K-3} Z ----
   for (int top = K - 3; top >= 0; top -= HV_CHUNK) {
     const int lowi = max(0, top - HV_CHUNK + 1);
-    for (int64_t f = tid; f < (int64_t)(top - lowi + 1) * K; f += EIG_THREADS) {
+    for (int64_t f = tid; f < (int64_t)(top - lowi + 1) * K; f += THREADS) {
       const int r = static_cast<int>(f / K), a = static_cast<int>(f % K);
       hv[r * K + a] = Hv[(int64_t)(lowi + r) * K + a];
     }
@@ -610,17 +600,17 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
         const int t = c0 + lane;
         float acc = 0.f;
         if (t < kw)
-          for (int a = wid; a < n; a += NW) acc = fmaf(v[a], Z[(int64_t)(i + 1 + a) * ldz + t], acc);
+          for (int a = wid; a < n; a += NWV) acc = fmaf(v[a], Z[(int64_t)(i + 1 + a) * ldz + t], acc);
         part[wid * 32 + lane] = acc;
         __syncthreads();
         if (tid < 32 && c0 + tid < kw) {
           float s = 0.f;
-          for (int w = 0; w < NW; ++w) s += part[w * 32 + tid];
+          for (int w = 0; w < NWV; ++w) s += part[w * 32 + tid];
           hvec[c0 + tid] = bt * s;
         }
         __syncthreads();
       }
-      for (int64_t f = tid; f < (int64_t)n * kw; f += EIG_THREADS) {
+      for (int64_t f = tid; f < (int64_t)n * kw; f += THREADS) {
         const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
         Z[(int64_t)(i + 1 + a) * ldz + t] -= v[a] * hvec[t];
       }
@@ -628,7 +618,7 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
     }
   }
 
-  for (int64_t f = tid; f < (int64_t)K * kw; f += EIG_THREADS) {
+  for (int64_t f = tid; f < (int64_t)K * kw; f += THREADS) {
     const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
     W[(int64_t)a * ld_w + t] = Z[(int64_t)a * ldz + t];
   }
@@ -787,6 +777,7 @@ struct TriCfg {
   int ppr, threads;
 };
 TriCfg tri_cfg(int K) {
+  if (K <= SMALL_K) return {8, 256};
   if (K - 1 <= 256) return {8, 1024};
   if (K - 1 <= 512) return {16, 1024};
   return {32, 512};
@@ -847,7 +838,8 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   const EigPlan pl = eig_plan(K, kw);
   MC_REQUIRE(pl.vec_smem <= EIG_SMEM && pl.tri_smem <= EIG_SMEM, "eig_topk: shared-memory plan does not fit");
   float *gw = static_cast<float *>(work);
-  MC_CUDA(cudaFuncSetAttribute(eig_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+  MC_CUDA(cudaFuncSetAttribute(eig_vectors_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+  MC_CUDA(cudaFuncSetAttribute(eig_vectors_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
   const TriCfg tc = tri_cfg(K);
   bool done = false;
   if (pl.coop) {
@@ -872,6 +864,9 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   }
 #define MC_TRI_ARGS K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta, gw + pl.g_hv, gw + pl.g_p, pl.p_in_smem
   if (done) {
+  } else if (tc.ppr == 8 && tc.threads == 256) {
+    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+    eig_tridiag_kernel<8, 256><<<1, 256, pl.tri_smem, st>>>(MC_TRI_ARGS);
   } else if (tc.ppr == 8) {
     MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
     eig_tridiag_kernel<8, 1024><<<1, 1024, pl.tri_smem, st>>>(MC_TRI_ARGS);
@@ -885,22 +880,27 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
 #undef MC_TRI_ARGS
   MC_CHECK_LAUNCH();
   if (K <= SPLIT_K) {
-    eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+    // small matrices: 256 threads (cheaper barriers), else 1024
+    if (K <= SMALL_K)
+      eig_vectors_kernel<256><<<1, 256, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                            gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_ALL);
+    else
+      eig_vectors_kernel<1024><<<1, 1024, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                             gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_ALL);
     MC_CHECK_LAUNCH();
     return;
   }
   // wide: multisection (one CTA), inverse iteration (a CTA per eigenvalue),
   // Gram-Schmidt (one CTA), back-transformation (a CTA per vector)
   float *Zg = gw + pl.vl.g_z;
-  eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+  eig_vectors_kernel<1024><<<1, 1024, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                          gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_BISECT);
   MC_CHECK_LAUNCH();
   const size_t ism = sizeof(float) * 7 * (size_t)K;
   MC_CUDA(cudaFuncSetAttribute(eig_invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(7 * 4 * 1024)));
   eig_invit_kernel<<<kw, 32, ism, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam, Zg, pl.vl.ldz);
   MC_CHECK_LAUNCH();
-  eig_vectors_kernel<<<1, EIG_THREADS, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+  eig_vectors_kernel<1024><<<1, 1024, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                          gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_GS);
   MC_CHECK_LAUNCH();
   eig_backtr_kernel<<<kw, BT_THREADS, sizeof(float) * (size_t)K, st>>>(K, gw + pl.g_beta, gw + pl.g_hv, Zg,

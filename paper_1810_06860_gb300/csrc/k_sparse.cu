@@ -36,17 +36,26 @@ __global__ void rowptr_check_kernel(int64_t m, int64_t nnz, const int64_t *__res
   }
 }
 
+// A warp per row, lanes along the row: every entry is compared with its
+// left neighbour in the row (long Zipf rows no longer run on one thread).
 __global__ void csr_check_kernel(int64_t m, int64_t n, const int *__restrict__ rp, const int *__restrict__ col,
                                  const float *__restrict__ val, int *__restrict__ flags) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  int prev = -1;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m) return;
+  const int b = rp[w], e1 = rp[w + 1];
+  int bad = 0, nonfin = 0;
+  for (int e = b + lane; e < e1; e += 32) {
     const int c = col[e];
-    if (c < 0 || c >= n) atomicOr(flags + 1, 1);
-    if (c <= prev) atomicOr(flags + 1, 2);
-    prev = c;
-    if (!isfinite(val[e])) atomicOr(flags + 2, 1);
+    if (c < 0 || c >= n) bad |= 1;
+    if (e > b && c <= col[e - 1]) bad |= 2;
+    if (!isfinite(val[e])) nonfin = 1;
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  nonfin = __reduce_or_sync(0xffffffffu, nonfin);
+  if (lane == 0) {
+    if (bad) atomicOr(flags + 1, bad);
+    if (nonfin) atomicOr(flags + 2, 1);
   }
 }
 
@@ -247,17 +256,19 @@ __global__ void to_bf16_kernel(int64_t rows, int cols, const float *__restrict__
   }
 }
 
+// A thread per (split row, column): the row's segment partials added in
+// segment order (the same order for every launch shape).
 __global__ void spmm_fixup_kernel(int64_t nsplit, const int *__restrict__ split_row,
                                   const int *__restrict__ split_slot, const float *__restrict__ partial, int K,
                                   float *__restrict__ out, int ld_out) {
-  const int64_t t = blockIdx.x;
-  if (t >= nsplit) return;
-  const int s0 = split_slot[t], s1 = split_slot[t + 1];
-  float *o = out + (int64_t)split_row[t] * ld_out;
-  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+  const int64_t total = nsplit * K;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / K;
+    const int c = static_cast<int>(t - i * K);
+    const int s0 = split_slot[i], s1 = split_slot[i + 1];
     float acc = 0.f;
-    for (int s = s0; s < s1; ++s) acc += partial[(int64_t)s * K + c];
-    o[c] = acc;
+    for (int sg = s0; sg < s1; ++sg) acc += partial[(int64_t)sg * K + c];
+    out[(int64_t)split_row[i] * ld_out + c] = acc;
   }
 }
 
@@ -379,7 +390,7 @@ inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
 void validate_csr(cudaStream_t st, int64_t m, int64_t n, const int *row_ptr, const int *col, const float *val,
                   int *flags) {
   if (m <= 0) return;
-  csr_check_kernel<<<grid_for(m, 256, 1 << 20), 256, 0, st>>>(m, n, row_ptr, col, val, flags);
+  csr_check_kernel<<<static_cast<unsigned>((m * 32 + 255) / 256), 256, 0, st>>>(m, n, row_ptr, col, val, flags);
   MC_CHECK_LAUNCH();
 }
 
@@ -530,7 +541,7 @@ void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val
 #undef MC_SEG_ARGS
     MC_CHECK_LAUNCH();
     if (plan.nsplit > 0) {
-      spmm_fixup_kernel<<<static_cast<unsigned>(plan.nsplit), 128, 0, st>>>(
+      spmm_fixup_kernel<<<grid_for(plan.nsplit * kc, 256), 256, 0, st>>>(
           plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, kc, out + c0, ld_out);
       MC_CHECK_LAUNCH();
     }
@@ -555,7 +566,7 @@ void spmm_bf16(cudaStream_t st, const SegPlan &plan, const int *idx, const float
 #undef MC_BF_ARGS
   MC_CHECK_LAUNCH();
   if (plan.nsplit > 0) {
-    spmm_fixup_kernel<<<static_cast<unsigned>(plan.nsplit), 128, 0, st>>>(
+    spmm_fixup_kernel<<<grid_for(plan.nsplit * K, 256), 256, 0, st>>>(
         plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, K, out, ld_out);
     MC_CHECK_LAUNCH();
   }

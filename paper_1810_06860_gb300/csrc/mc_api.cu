@@ -152,6 +152,7 @@ struct mc_handle_s {
   DBuf flags;
   // rSVD result bookkeeping
   int Kq = 0;          // columns of the basis whose Ritz pairs are in W (incl. zero padding)
+  int bt_ready = 0;    // leading columns of Bt = Y^T Q already formed by the Krylov loop
   int q_real = 0;      // real (non-padding) columns of the stored Krylov basis
   int kw = 0;          // eigenpairs in lam/W
   std::vector<float> h_lam;
@@ -482,6 +483,10 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
   float *Q = fbuf(h, h->Q, (size_t)h->m * ktp);
   float *H = fbuf(h, h->H, (size_t)h->m * kbp);
   float *T = fbuf(h, h->T, (size_t)h->n * kbp);
+  // plain form: Y^T Q_{i-1} of step i is column block i-1 of B^T = Y^T Q (the
+  // Ritz step then forms only the last block)
+  float *Bt = mixed ? nullptr : fbuf(h, h->Bt, (size_t)h->n * ktp);
+  h->bt_ready = 0;
   if (mixed) spmm_Y_bf(h, bf_panel(h, h->Om_bf, h->n, kbp, h->Om.as<float>(), kbp), kbp, H, kbp);
   else spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // H_0 = A Omega
   if (!orth_block_fused(h, h->m, kbp, H, kbp, nullptr, 0, 0, Q, ktp)) orth_block(h, h->m, kbp, H, kbp, Q, ktp);
@@ -490,8 +495,9 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
       spmm_Yt_bf(h, bf_panel(h, h->Q_bf, h->m, kbp, Q + (size_t)(i - 1) * kbp, ktp), kbp, T, kbp);
       spmm_Y_bf(h, bf_panel(h, h->T_bf, h->n, kbp, T, kbp), kbp, H, kbp);
     } else {
-      spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, T, kbp);  // A^T Q_{i-1}
-      spmm_Y(h, T, kbp, kbp, H, kbp);                          // A (A^T Q_{i-1})
+      float *Ti = Bt + (size_t)(i - 1) * kbp;
+      spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, Ti, ktp);  // A^T Q_{i-1}
+      spmm_Y(h, Ti, ktp, kbp, H, kbp);                           // A (A^T Q_{i-1})
     }
     if (orth_block_fused(h, h->m, kbp, H, kbp, Q, ktp, i * kbp, Q + (size_t)i * kbp, ktp)) continue;
     float *ref = fbuf(h, h->lam, (size_t)kbp + colsumsq_scratch_floats(kbp));
@@ -501,6 +507,7 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
   }
   h->Kq = ktp;
   h->q_real = (p + 1) * kb;
+  h->bt_ready = mixed ? 0 : p * kbp;
 }
 
 // Power-iteration basis of Alg. 4 (steps 1-7) into h->Q (m x kbp).
@@ -530,11 +537,13 @@ void power_pi(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id) {
 
 // Steps 8-10 of Alg. 5 with basis Qb (m x Kq): B^T = A^T Qb, G = B B^T,
 // top-kw eigenpairs (values to the host).
-void ritz(mc_handle h, const float *Qb, int ldq, int Kq, int kw) {
+void ritz(mc_handle h, const float *Qb, int ldq, int Kq, int kw, bool fresh_krylov = false) {
   MC_REQUIRE(Kq <= kMaxKt, "basis wider than 1024");
   kw = std::min(kw, Kq);
-  float *Bt = fbuf(h, h->Bt, (size_t)h->n * Kq);
-  spmm_Yt(h, Qb, ldq, Kq, Bt, Kq);
+  const int ready = fresh_krylov && ldq == Kq ? std::min(h->bt_ready, Kq) : 0;
+  h->bt_ready = 0;
+  float *Bt = ready > 0 ? h->Bt.as<float>() : fbuf(h, h->Bt, (size_t)h->n * Kq);
+  spmm_Yt(h, Qb + ready, ldq, Kq - ready, Bt + ready, Kq);
   float *G = fbuf(h, h->G, (size_t)Kq * Kq);
   gram(h, h->n, Kq, Bt, Kq, G, Kq);
   float *lam = fbuf(h, h->lam, (size_t)Kq);
@@ -603,7 +612,7 @@ mc_status do_rsvd(mc_handle h, bool bki, int k, int s, int p, uint64_t seed, uin
   const int kb = k + s;
   if (bki) krylov_bki(h, kb, p, seed, call_id, nullptr, 0, 0);
   else power_pi(h, kb, p, seed, call_id);
-  ritz(h, h->Q.as<float>(), h->Kq, h->Kq, k);
+  ritz(h, h->Q.as<float>(), h->Kq, h->Kq, k, bki);
   std::vector<double> sig;
   const int kk = ritz_sigmas(h, k, sig);
   const int ldp = (int)round_up(std::max(kk, 1), 4);
@@ -703,7 +712,7 @@ void svt_svd(mc_handle h, int kk, int pp, bool fresh, std::vector<double> &sig, 
     }
     krylov_bki(h, kk + P.s, pp, P.seed, h->call_id, warm, h->vb_ld, wcols);
     h->call_id += 1;
-    ritz(h, h->Q.as<float>(), h->Kq, h->Kq, kk);
+    ritz(h, h->Q.as<float>(), h->Kq, h->Kq, kk, true);
     *Qb = h->Q.as<float>();
     *ldq = h->Kq;
     if (P.recycle == 1) h->basis = 1;
