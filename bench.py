@@ -174,6 +174,24 @@ def barrier(world):
         dist.barrier()
 
 
+def max_over_ranks(t_ms: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time (the job's time): replicas run independently and
+    meet only here, after the timed region."""
+    if world <= 1:
+        return t_ms
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank: int, world: int, t_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (t_ms / 1e3)
+
+
 def svt_params(mc, o):
     return mc.params(tau=5.0 * math.sqrt(o.m * o.n), delta=DELTA, eps=1e-4, recycle=1, i_reuse=50, q_reuse=10,
                      seed=SEED)
@@ -248,13 +266,8 @@ def run_ours(args, rank, world, local):
     t_ms = e0.elapsed_time(e1)
     tm = h.timing_read()
     h.timing_enable(False)
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = args.steps * world / (t_ms / 1e3)
+    t_ms = max_over_ranks(t_ms, world)
+    value = job_rate(args.steps, world, t_ms)
     # held-out RMSE of the estimate after the timed iterations
     pred = h.sample(o.test_rows, o.test_cols)
     rmse = float(np.sqrt(np.mean((pred.astype(np.float64) - o.test_val) ** 2)))

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <cstdlib>
 #include <mutex>
 
 namespace mc {
@@ -1039,8 +1040,7 @@ static size_t on_smem(int64_t rows_per, int K, int cols) {
 }
 
 bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
-                 int ldo, const float *ref_unused, bool use_ref, float shift_rel, float ref_tol, float *scratch) {
-  (void)ref_unused;
+                 int ldo, bool use_ref, float shift_rel, float ref_tol, float *scratch) {
   if (K < 1 || K > ON_MAXK || R < 1 || cols < 0) return false;
   if (((cols + 3) / 4) * ((K + 3) / 4) > ON_THREADS) return false;  // one 4 x 4 tile of Qp^T X per thread at most
   int dev = 0, sms = 0, coop = 0;
@@ -1054,7 +1054,12 @@ bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const flo
   MC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   // CTAs: one to four per SM, at least 32 rows each, the rows and the
   // panel slices of a CTA in at most 220 KB / CTAs-per-SM of shared memory
-  for (int per_sm = 4; per_sm >= 1; --per_sm) {
+  // (MC_ORTH_PER_SM caps the CTAs per SM)
+  static const int cap = [] {
+    const char *v = std::getenv("MC_ORTH_PER_SM");
+    return v ? std::max(1, std::min(4, std::atoi(v))) : 4;
+  }();
+  for (int per_sm = cap; per_sm >= 1; --per_sm) {
     const int64_t nb = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (R + 31) / 32));
     const int64_t rows_per = (R + nb - 1) / nb;
     const size_t smem = on_smem(rows_per, K, cols);

@@ -135,7 +135,6 @@ struct Prof {
 }  // namespace
 
 struct mc_handle_s {
-  ~mc_handle_s() = default;
   int64_t m = 0, n = 0, nnz = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -471,7 +470,7 @@ bool orth_block_fused(mc_handle h, int64_t R, int K, float *X, int ldx, const fl
   if (!on || K > 32) return false;
   float *scr = fbuf(h, h->tn_part, orth_narrow_scratch_floats(R, K, cols));
   Scope sc(h, MC_T_GEMM, 4.0 * R * (2.0 * K + cols), 2.0 * R * K * (2.0 * cols + 1.5 * K));
-  return orth_narrow(h->stream, R, K, X, ldx, Qp, ldq, cols, out, ldo, nullptr, cols > 0, 1e-6f, 1e-10f, scr);
+  return orth_narrow(h->stream, R, K, X, ldx, Qp, ldq, cols, out, ldo, cols > 0, 1e-6f, 1e-10f, scr);
 }
 
 void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, const float *warm, int warm_ld,
@@ -482,23 +481,19 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
   draw_omega(h, kb, kbp, seed, call_id, warm, warm_ld, warm_cols);
   float *Q = fbuf(h, h->Q, (size_t)h->m * ktp);
   float *H = fbuf(h, h->H, (size_t)h->m * kbp);
-  float *T = fbuf(h, h->T, (size_t)h->n * kbp);
-  // plain form: Y^T Q_{i-1} of step i is column block i-1 of B^T = Y^T Q (the
-  // Ritz step then forms only the last block)
-  float *Bt = mixed ? nullptr : fbuf(h, h->Bt, (size_t)h->n * ktp);
+  // Y^T Q_{i-1} of step i (float32 in both forms) is column block i-1 of
+  // B^T = Y^T Q, so the Ritz step forms only the last block; the mixed form
+  // rounds only the panel of the following Y (Y^T Q_{i-1}) product to bf16
+  float *Bt = fbuf(h, h->Bt, (size_t)h->n * ktp);
   h->bt_ready = 0;
   if (mixed) spmm_Y_bf(h, bf_panel(h, h->Om_bf, h->n, kbp, h->Om.as<float>(), kbp), kbp, H, kbp);
   else spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // H_0 = A Omega
   if (!orth_block_fused(h, h->m, kbp, H, kbp, nullptr, 0, 0, Q, ktp)) orth_block(h, h->m, kbp, H, kbp, Q, ktp);
   for (int i = 1; i <= p; ++i) {
-    if (mixed) {
-      spmm_Yt_bf(h, bf_panel(h, h->Q_bf, h->m, kbp, Q + (size_t)(i - 1) * kbp, ktp), kbp, T, kbp);
-      spmm_Y_bf(h, bf_panel(h, h->T_bf, h->n, kbp, T, kbp), kbp, H, kbp);
-    } else {
-      float *Ti = Bt + (size_t)(i - 1) * kbp;
-      spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, Ti, ktp);  // A^T Q_{i-1}
-      spmm_Y(h, Ti, ktp, kbp, H, kbp);                           // A (A^T Q_{i-1})
-    }
+    float *Ti = Bt + (size_t)(i - 1) * kbp;
+    spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, Ti, ktp);  // A^T Q_{i-1}
+    if (mixed) spmm_Y_bf(h, bf_panel(h, h->T_bf, h->n, kbp, Ti, ktp), kbp, H, kbp);
+    else spmm_Y(h, Ti, ktp, kbp, H, kbp);                     // A (A^T Q_{i-1})
     if (orth_block_fused(h, h->m, kbp, H, kbp, Q, ktp, i * kbp, Q + (size_t)i * kbp, ktp)) continue;
     float *ref = fbuf(h, h->lam, (size_t)kbp + colsumsq_scratch_floats(kbp));
     colsumsq(h->stream, h->m, kbp, H, kbp, ref, ref + kbp);
@@ -507,7 +502,7 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
   }
   h->Kq = ktp;
   h->q_real = (p + 1) * kb;
-  h->bt_ready = mixed ? 0 : p * kbp;
+  h->bt_ready = p * kbp;
 }
 
 // Power-iteration basis of Alg. 4 (steps 1-7) into h->Q (m x kbp).

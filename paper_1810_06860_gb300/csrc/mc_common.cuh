@@ -182,7 +182,7 @@ void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *
 // has no cooperative launch; the caller then takes the separate kernels.
 size_t orth_narrow_scratch_floats(int64_t R, int K, int cols);
 bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
-                 int ldo, const float *ref_unused, bool use_ref, float shift_rel, float ref_tol, float *scratch);
+                 int ldo, bool use_ref, float shift_rel, float ref_tol, float *scratch);
 size_t gram_tc_scratch_floats(int64_t R, int K);
 bool gram_tc_supported(int K, int ld, const void *X);
 void gram_tc(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *G, int ld_g, float *partial, int *err);
