@@ -230,7 +230,7 @@ def run_ours(args, rank, world, local):
         hb.rsvd_bki(K_BKI, S_OVER, P_BKI, seed=SEED, call_id=i, device=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nb = 10
+    nb = 20
     e0.record(stream)
     for i in range(nb):
         hb.rsvd_bki(K_BKI, S_OVER, P_BKI, seed=SEED, call_id=100 + i, device=True)
@@ -241,6 +241,19 @@ def run_ours(args, rank, world, local):
     hb.rsvd_bki(K_BKI, S_OVER, P_BKI, seed=SEED, call_id=200, device=True)
     bki_tm = {k: round(v["ms"], 3) for k, v in hb.timing_read().items()}
     hb.timing_enable(False)
+    # the other two randomized SVDs on the same matrix: rSVD-PI (Alg. 4) with
+    # the same p, and basic rSVD (Alg. 1 = Alg. 4 with p = 0)
+    other_ms = {}
+    for name, pp in (("rsvd_pi_ms", P_BKI), ("rsvd_basic_ms", 0)):
+        for i in range(3):
+            hb.rsvd_pi(K_BKI, S_OVER, pp, seed=SEED, call_id=300 + i, device=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(nb):
+            hb.rsvd_pi(K_BKI, S_OVER, pp, seed=SEED, call_id=400 + i, device=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        other_ms[name] = round(e0.elapsed_time(e1) / nb, 3)
     hb.close()
     del rp, ci, va
     # ---- SVT iterations -----------------------------------------------------
@@ -360,7 +373,7 @@ def run_ours(args, rank, world, local):
                            timed_iterations=f"{args.warmup + 1}..{args.warmup + args.steps}",
                            k_last=last["k"], r_last=last["r"], p_last=last["p"], err_last=round(last["err"], 6),
                            heldout_rmse=round(rmse, 5)),
-            "rsvd_bki_ms": round(bki_ms, 3), "rsvd_bki_timing_ms": bki_tm, "mixed_precision": mixed, "serving": serving,
+            "rsvd_bki_ms": round(bki_ms, 3), "rsvd_bki_timing_ms": bki_tm, **other_ms, "mixed_precision": mixed, "serving": serving,
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(), "gpu_launches": int(launches),
             "timing_ms": {k: round(v["ms"], 3) for k, v in tm.items()}}
@@ -401,6 +414,12 @@ def run_serving(mc, num_jobs: int):
         wall = time.perf_counter() - t0
         st = srv.stats()
     lat = np.array([r["latency_s"] for r in res])
+    # jobs that do not reach eps (too few samples for their rank) run to i_max
+    # and set the tail; converged and unconverged jobs are reported apart
+    rec = np.array([bool(r["converged"]) for r in res])
+    dof = np.array([j["rank"] * (j["m"] + j["n"] - j["rank"]) for j in spec])
+    def pct(x, q):
+        return round(float(np.percentile(x, q)), 4) if len(x) else None
     held = []
     for o, r in zip(obs, res):
         if r.get("Us") is None:
@@ -415,6 +434,12 @@ def run_serving(mc, num_jobs: int):
     return {"solves_per_s": round(len(res) / wall, 3), "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
             "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
             "p50_queue_s": round(float(np.percentile([r["queue_s"] for r in res], 50)), 4),
+            "converged_jobs": {"jobs": int(rec.sum()), "p50_latency_s": pct(lat[rec], 50),
+                               "p99_latency_s": pct(lat[rec], 99),
+                               "median_samples_per_dof": pct((np.array(nnz) / dof)[rec], 50)},
+            "unconverged_jobs": {"jobs": int((~rec).sum()), "p50_latency_s": pct(lat[~rec], 50),
+                                 "p99_latency_s": pct(lat[~rec], 99),
+                                 "median_samples_per_dof": pct((np.array(nnz) / dof)[~rec], 50)},
             "jobs": len(res), "converged": int(sum(r["converged"] for r in res)),
             "iters_total": int(sum(r["iters"] for r in res)), "nnz_total": int(sum(nnz)),
             "median_rel_rmse_unobserved": round(float(np.median(held)), 5) if held else None,

@@ -110,6 +110,12 @@ const char *mc_status_str(mc_status s);
  * of range or non-finite values; MC_ENOMEM; MC_ECUDA. */
 mc_status mc_create(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
                     const int32_t *col, const float *val, void *stream, const mc_allocator *alloc);
+/* mc_create_coo: as mc_create, from coordinates in any order: rows int64[nnz],
+ * cols int32[nnz], vals float32[nnz] (host or device).  The entries are
+ * sorted on the device by (row, column) with a stable radix sort into the CSR
+ * that mc_create takes.  MC_EINVAL also for a repeated (row, column) pair. */
+mc_status mc_create_coo(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int64_t *rows,
+                        const int32_t *cols, const float *vals, void *stream, const mc_allocator *alloc);
 void mc_destroy(mc_handle h);
 
 /* Set the values of the sparse iterate Y (CSR order, nnz floats, host or

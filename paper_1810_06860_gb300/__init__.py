@@ -129,6 +129,26 @@ class Handle:
     def from_observed(cls, obs, **kw):
         return cls(obs.m, obs.n, obs.row_ptr, obs.col, obs.val, **kw)
 
+    @classmethod
+    def from_coo(cls, m: int, n: int, rows, cols, vals, stream=None):
+        """Observed entries as coordinates in any order (mc_create_coo)."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        self.m, self.n = int(m), int(n)
+        r, k1 = _ptr(rows, np.int64)
+        c, k2 = _ptr(cols, np.int32)
+        v, k3 = _ptr(vals, np.float32)
+        self.nnz = int(len(cols))
+        self._alloc = None
+        st_ptr = None
+        if stream is not None:
+            st_ptr = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        h = C.c_void_p()
+        _check(lib.mc_create_coo(C.byref(h), self.m, self.n, self.nnz, r, c, v, st_ptr, None), "mc_create_coo")
+        self._h = h
+        return self
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.mc_destroy(self._h)

@@ -63,6 +63,7 @@ _SIGS = {
     "mc_launch_count": (C.c_int64, []),
     "mc_status_str": (C.c_char_p, [C.c_int]),
     "mc_create": (C.c_int, [C.POINTER(_P), C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, _P, C.POINTER(McAllocator)]),
+    "mc_create_coo": (C.c_int, [C.POINTER(_P), C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, _P, C.POINTER(McAllocator)]),
     "mc_destroy": (None, [_P]),
     "mc_set_values": (C.c_int, [_P, _P]),
     "mc_get_values": (C.c_int, [_P, _P]),

@@ -100,8 +100,15 @@ struct TnSmall {
 template <int T>
 __global__ void __launch_bounds__(256)
 gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ Y,
-                     int ld_y, int64_t rows_per_split, int sym, int same, float *__restrict__ partial) {
+                     int ld_y, int64_t rows_per_split, int sym, int same, float *__restrict__ partial, int tiles_j,
+                     int K1p, int K2p) {
   using P = TnSmall<T>;
+  // output tile (ti, tj) of blockIdx.y; below-diagonal tiles of a Gram are mirrored by the reducer
+  const int ti = blockIdx.y / tiles_j, tj = blockIdx.y % tiles_j;
+  if (sym && tj < ti) return;
+  const int i0 = ti * T, j0 = tj * T;
+  X += i0;
+  Y += j0;
   extern __shared__ __align__(16) float tns[];
   float *xs = tns;                                          // [STAGES][CH][T]
   float *ys = same ? tns : tns + TNS_STAGES * P::CH * T;    // [STAGES][CH][T]
@@ -116,10 +123,10 @@ gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
     for (int e = tid; e < P::CH * P::TQ; e += 256) {
       const int rr = e / P::TQ, c4 = (e % P::TQ) * 4;
       const int64_t r = rb + rr;
-      const bool okx = r < r1 && c4 < K1;
+      const bool okx = r < r1 && i0 + c4 < K1;
       cp_async16(xs + ((size_t)stg * P::CH + rr) * T + c4, okx ? X + r * ld_x + c4 : X, okx ? 16 : 0);
       if (!same) {
-        const bool oky = r < r1 && c4 < K2;
+        const bool oky = r < r1 && j0 + c4 < K2;
         cp_async16(ys + ((size_t)stg * P::CH + rr) * T + c4, oky ? Y + r * ld_y + c4 : Y, oky ? 16 : 0);
       }
     }
@@ -129,7 +136,7 @@ gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
     if (c < nchunks) issue(c);
     cp_async_commit();
   }
-  const bool active = ty * 4 < K1 && tx * 4 < K2 && !(sym && ty > tx);
+  const bool active = i0 + ty * 4 < K1 && j0 + tx * 4 < K2 && !(sym && ti == tj && ty > tx);
   float acc[4][4] = {};
   for (int c = 0; c < nchunks; ++c) {
     if (c + TNS_STAGES - 1 < nchunks) issue(c + TNS_STAGES - 1);
@@ -153,11 +160,12 @@ gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
     __syncthreads();
   }
   cp_async_wait<0>();
-  float *dst = partial + (int64_t)blockIdx.x * T * T;
+  float *dst = partial + (int64_t)blockIdx.x * K1p * K2p + (int64_t)i0 * K2p + j0;
   if (P::G == 1) {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      *reinterpret_cast<float4 *>(dst + (ty * 4 + u) * T + tx * 4) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+      *reinterpret_cast<float4 *>(dst + (int64_t)(ty * 4 + u) * K2p + tx * 4) =
+          make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
     return;
   }
   float *red = tns;  // [G][T][T], fits in the stage buffers
@@ -171,7 +179,7 @@ gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
     float v = 0.f;
 #pragma unroll
     for (int gg = 0; gg < P::G; ++gg) v += red[(size_t)gg * T * T + e];
-    dst[e] = v;
+    dst[(int64_t)(e / T) * K2p + e % T] = v;
   }
 }
 
@@ -211,64 +219,73 @@ gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ part
   }
 }
 
-// ---- gemm_nn for narrow panels (K1, K2 <= 64) -------------------------------
-// W (zero-padded to 64 x 64) stays in shared memory; 64-row chunks of X
-// stream through three cp.async buffers.  Thread (ty, tx) computes rows
-// 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 of the chunk's output.
-constexpr int NNS_BM = 64, NNS_STAGES = 3;
-constexpr size_t kNnSmallSmem = sizeof(float) * (64 * 64 + NNS_STAGES * NNS_BM * 64);
+// ---- gemm_nn with the small factor in shared memory (K1 <= 256) -------------
+// W (its K1 x 64 column slice for output columns j0 .. j0+63, zero-padded)
+// stays in shared memory; 64-row chunks of X stream through cp.async
+// buffers (three for K1 <= 64, two above).  Thread (ty, tx) computes rows
+// 4 ty .. 4 ty + 3 and columns j0 + 4 tx .. + 3 of the chunk's output.
+constexpr int NNS_BM = 64;
+template <int KM1>
+struct NnSmall {
+  static constexpr int STAGES = KM1 <= 64 ? 3 : 2;
+  static constexpr int LDX = KM1 + 4;  // padded row: the two row groups of a warp hit different banks
+  static constexpr size_t smem = sizeof(float) * ((size_t)KM1 * 64 + (size_t)STAGES * NNS_BM * LDX);
+};
 
+template <int KM1>
 __global__ void __launch_bounds__(256)
 gemm_nn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ W,
                      int ld_w, const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z,
                      int ld_z, int64_t chunks_per_block) {
+  using P = NnSmall<KM1>;
   extern __shared__ __align__(16) float nns[];
-  float *ws = nns;            // [64][64]
-  float *xs = nns + 64 * 64;  // [STAGES][BM][64]
+  float *ws = nns;                   // [KM1][64]
+  float *xs = nns + KM1 * 64;        // [STAGES][BM][LDX]
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int j0 = blockIdx.y * 64;
   const int64_t nch_total = (R + NNS_BM - 1) / NNS_BM;
   const int64_t c0 = (int64_t)blockIdx.x * chunks_per_block;
   const int64_t c1 = min(nch_total, c0 + chunks_per_block);
   const int nch = c1 > c0 ? static_cast<int>(c1 - c0) : 0;
   const int K4 = (K1 + 3) / 4;
   auto issue = [&](int c) {
-    const int stg = c % NNS_STAGES;
+    const int stg = c % P::STAGES;
     const int64_t rb = (c0 + c) * NNS_BM;
-    for (int e = tid; e < NNS_BM * 16; e += 256) {
-      const int rr = e / 16, k4 = (e % 16) * 4;
+    for (int e = tid; e < NNS_BM * (KM1 / 4); e += 256) {
+      const int rr = e / (KM1 / 4), k4 = (e % (KM1 / 4)) * 4;
       const int64_t r = rb + rr;
       const bool ok = r < R && k4 < K1;
-      cp_async16(xs + ((size_t)stg * NNS_BM + rr) * 64 + k4, ok ? X + r * ld_x + k4 : X, ok ? 16 : 0);
+      cp_async16(xs + ((size_t)stg * NNS_BM + rr) * P::LDX + k4, ok ? X + r * ld_x + k4 : X, ok ? 16 : 0);
     }
   };
 #pragma unroll
-  for (int c = 0; c < NNS_STAGES - 1; ++c) {
+  for (int c = 0; c < P::STAGES - 1; ++c) {
     if (c < nch) issue(c);
     cp_async_commit();
   }
-  for (int e = tid; e < 64 * 64; e += 256) {
+  for (int e = tid; e < KM1 * 64; e += 256) {
     const int k = e / 64, j = e % 64;
-    ws[e] = (k < K1 && j < K2) ? W[(int64_t)k * ld_w + j] : 0.f;
+    ws[e] = (k < K1 && j0 + j < K2) ? W[(int64_t)k * ld_w + j0 + j] : 0.f;
   }
   float sc[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const int j = tx * 4 + v;
+    const int j = j0 + tx * 4 + v;
     sc[v] = j < K2 ? alpha * (colscale ? colscale[j] : 1.0f) : 0.f;
   }
-  const bool vec_out = (ld_z % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0) && tx * 4 + 3 < K2;
+  const bool vec_out = (ld_z % 4 == 0) && ((reinterpret_cast<uintptr_t>(Z) & 15u) == 0) && j0 + tx * 4 + 3 < K2;
   for (int c = 0; c < nch; ++c) {
-    if (c + NNS_STAGES - 1 < nch) issue(c + NNS_STAGES - 1);
+    if (c + P::STAGES - 1 < nch) issue(c + P::STAGES - 1);
     cp_async_commit();
-    cp_async_wait<NNS_STAGES - 1>();
+    cp_async_wait<P::STAGES - 1>();
     __syncthreads();
-    const float *xb = xs + (size_t)(c % NNS_STAGES) * NNS_BM * 64;
+    const float *xb = xs + (size_t)(c % P::STAGES) * NNS_BM * P::LDX;
     float acc[4][4] = {};
-    if (tx * 4 < K2) {
+    if (j0 + tx * 4 < K2) {
       for (int k4 = 0; k4 < K4; ++k4) {
         float4 a[4], b[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = *reinterpret_cast<const float4 *>(xb + (ty * 4 + u) * 64 + k4 * 4);
+        for (int u = 0; u < 4; ++u) a[u] = *reinterpret_cast<const float4 *>(xb + (ty * 4 + u) * P::LDX + k4 * 4);
 #pragma unroll
         for (int t = 0; t < 4; ++t) b[t] = *reinterpret_cast<const float4 *>(ws + (k4 * 4 + t) * 64 + tx * 4);
 #pragma unroll
@@ -288,21 +305,21 @@ gemm_nn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
       for (int u = 0; u < 4; ++u) {
         const int64_t r = rb + ty * 4 + u;
         if (r >= R) continue;
-        float *z = Z + r * ld_z + tx * 4;
+        float *z = Z + r * ld_z + j0 + tx * 4;
         if (vec_out) {
           float4 o = make_float4(acc[u][0] * sc[0], acc[u][1] * sc[1], acc[u][2] * sc[2], acc[u][3] * sc[3]);
           if (beta != 0.f) {
-            const float4 p = *reinterpret_cast<const float4 *>(z);
-            o.x += beta * p.x;
-            o.y += beta * p.y;
-            o.z += beta * p.z;
-            o.w += beta * p.w;
+            const float4 pz = *reinterpret_cast<const float4 *>(z);
+            o.x += beta * pz.x;
+            o.y += beta * pz.y;
+            o.z += beta * pz.z;
+            o.w += beta * pz.w;
           }
           *reinterpret_cast<float4 *>(z) = o;
         } else {
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            if (tx * 4 + v >= K2) continue;
+            if (j0 + tx * 4 + v >= K2) continue;
             z[v] = (beta != 0.f ? beta * z[v] : 0.f) + acc[u][v] * sc[v];
           }
         }
@@ -905,40 +922,48 @@ void select_cols(cudaStream_t st, int K, const float *W, int ld_w, int ncols, in
   MC_CHECK_LAUNCH();
 }
 
-static int tn_splits(int64_t R, int tiles) {
-  const int64_t want = std::max<int64_t>(1, (152 * 2 + tiles - 1) / std::max(tiles, 1));
-  const int64_t max_by_rows = std::max<int64_t>(1, R / 256);
-  return static_cast<int>(std::min<int64_t>(std::min<int64_t>(want, max_by_rows), 1024));
-}
-
-// narrow panels: tile edge of the small kernel (0: use the tiled kernel)
+// tile edge of the pipelined kernel: one T x T tile for narrow panels,
+// 64 x 64 tiles (a grid of them) for wider ones
 static int tn_small_tile(int K1, int K2) {
   const int k = std::max(K1, K2);
-  return k <= 16 ? 16 : (k <= 32 ? 32 : (k <= 64 ? 64 : 0));
+  return k <= 16 ? 16 : (k <= 32 ? 32 : 64);
 }
-static int tn_small_splits(int64_t R) {
-  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(304, (R + 63) / 64)));
+struct TnPlan {
+  int T, K1p, K2p, tiles_i, tiles_j, nsplit;
+  int64_t rps;
+};
+static TnPlan tn_plan(int64_t R, int K1, int K2, bool sym) {
+  TnPlan pl{};
+  pl.T = tn_small_tile(K1, K2);
+  pl.K1p = (int)round_up(std::max(K1, 1), pl.T);
+  pl.K2p = (int)round_up(std::max(K2, 1), pl.T);
+  pl.tiles_i = pl.K1p / pl.T;
+  pl.tiles_j = pl.K2p / pl.T;
+  const int active = sym ? pl.tiles_i * (pl.tiles_i + 1) / 2 : pl.tiles_i * pl.tiles_j;
+  const int64_t want = std::max<int64_t>(1, (304 + active - 1) / active);
+  const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(want, (R + 63) / 64));
+  pl.rps = round_up((R + ns - 1) / ns, 64);
+  pl.nsplit = static_cast<int>((R + pl.rps - 1) / pl.rps);
+  return pl;
 }
 
 size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2) {
-  const int T = tn_small_tile(K1, K2);
-  if (T) return (size_t)tn_small_splits(R) * T * T;
-  const int K1p = (int)round_up(std::max(K1, 1), TN_T), K2p = (int)round_up(std::max(K2, 1), TN_T);
-  const int tiles = (K1p / TN_T) * (K2p / TN_T);
-  return (size_t)tn_splits(R, tiles) * K1p * K2p;
+  // the largest plan over sym / non-sym (sym has fewer active tiles, more splits)
+  const TnPlan a = tn_plan(R, K1, K2, true), b = tn_plan(R, K1, K2, false);
+  return std::max((size_t)a.nsplit * a.K1p * a.K2p, (size_t)b.nsplit * b.K1p * b.K2p);
 }
 
 template <int T>
 static void launch_tn_small(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y,
-                            int ld_y, bool sym, float *partial, int nsplit, int64_t rps) {
-  const bool same = (X == Y && ld_x == ld_y && K1 == K2);
+                            int ld_y, bool symg, bool same, float *partial, const TnPlan &pl) {
   const size_t smem = TnSmall<T>::smem_bytes(same);
   // the attribute is per kernel and process-wide: always set the largest size
   // any call needs, so concurrent callers on other threads never lower it
   MC_CUDA(cudaFuncSetAttribute(gemm_tn_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)TnSmall<T>::smem_bytes(false)));
-  gemm_tn_small_kernel<T><<<nsplit, 256, smem, st>>>(R, K1, K2, X, ld_x, Y, ld_y, rps, (sym && same) ? 1 : 0,
-                                                     same ? 1 : 0, partial);
+  dim3 grid((unsigned)pl.nsplit, (unsigned)(pl.tiles_i * pl.tiles_j));
+  gemm_tn_small_kernel<T><<<grid, 256, smem, st>>>(R, K1, K2, X, ld_x, Y, ld_y, pl.rps, symg ? 1 : 0, same ? 1 : 0,
+                                                   partial, pl.tiles_j, pl.K1p, pl.K2p);
   MC_CHECK_LAUNCH();
 }
 
@@ -946,32 +971,17 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
              int ld_c, bool sym, float *partial) {
   if (K1 <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0 && ld_y % 4 == 0, "gemm_tn: leading dims must be multiples of 4");
-  const int T = tn_small_tile(K1, K2);
-  if (T) {
-    MC_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0,
-               "gemm_tn: panels must be 16-byte aligned");
-    const int nsplit = tn_small_splits(R);
-    const int64_t rps = round_up((R + nsplit - 1) / nsplit, 64);
-    const int ns = static_cast<int>((R + rps - 1) / rps);
-    if (T == 16) launch_tn_small<16>(st, R, K1, K2, X, ld_x, Y, ld_y, sym, partial, ns, rps);
-    else if (T == 32) launch_tn_small<32>(st, R, K1, K2, X, ld_x, Y, ld_y, sym, partial, ns, rps);
-    else launch_tn_small<64>(st, R, K1, K2, X, ld_x, Y, ld_y, sym, partial, ns, rps);
-    const int64_t total = (int64_t)K1 * K2;
-    const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
-    gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, ns, partial, T, T, sym && X == Y, 4, C, ld_c);
-    MC_CHECK_LAUNCH();
-    return;
-  }
-  const int K1p = (int)round_up(K1, TN_T), K2p = (int)round_up(K2, TN_T);
-  const int ti = K1p / TN_T, tj = K2p / TN_T;
-  const int nsplit = tn_splits(R, ti * tj);
-  const int64_t rps = round_up((R + nsplit - 1) / nsplit, TN_RB);
-  dim3 grid(ti * tj, nsplit);
-  gemm_tn_kernel<<<grid, 256, 0, st>>>(R, K1, K2, X, ld_x, Y, ld_y, rps, tj, sym, partial, K1p, K2p);
-  MC_CHECK_LAUNCH();
+  MC_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0,
+             "gemm_tn: panels must be 16-byte aligned");
+  const bool same = (X == Y && ld_x == ld_y && K1 == K2);
+  const bool symg = sym && same;  // only a true Gram skips the lower tiles
+  const TnPlan pl = tn_plan(R, K1, K2, symg);
+  if (pl.T == 16) launch_tn_small<16>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl);
+  else if (pl.T == 32) launch_tn_small<32>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl);
+  else launch_tn_small<64>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl);
   const int64_t total = (int64_t)K1 * K2;
   const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
-  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, nsplit, partial, K1p, K2p, sym, TN_T, C, ld_c);
+  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, pl.nsplit, partial, pl.K1p, pl.K2p, symg, 4, C, ld_c);
   MC_CHECK_LAUNCH();
 }
 
@@ -979,13 +989,26 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
              const float *colscale, float alpha, float beta, float *Z, int ld_z) {
   if (R <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0, "gemm_nn: ld_x must be a multiple of 4");
-  if (K1 <= 64 && K2 <= 64 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+  if (K1 <= 256 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
     const int64_t nch = (R + NNS_BM - 1) / NNS_BM;
-    const int64_t per = std::max<int64_t>(1, (nch + 152 * 3 - 1) / (152 * 3));
-    const unsigned nb = static_cast<unsigned>((nch + per - 1) / per);
-    MC_CUDA(cudaFuncSetAttribute(gemm_nn_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNnSmallSmem));
-    gemm_nn_small_kernel<<<nb, 256, kNnSmallSmem, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, Z, ld_z,
-                                                        per);
+    const int tiles = (K2 + 63) / 64;
+    const int per_sm = K1 <= 64 ? 3 : (K1 <= 128 ? 2 : 1);
+    const int64_t want = std::max<int64_t>(1, (int64_t)152 * per_sm / tiles);
+    const int64_t per = std::max<int64_t>(1, (nch + want - 1) / want);
+    const dim3 grid(static_cast<unsigned>((nch + per - 1) / per), static_cast<unsigned>(tiles));
+#define MC_NN_SMALL(KM)                                                                                              \
+  MC_CUDA(cudaFuncSetAttribute(gemm_nn_small_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+                               (int)NnSmall<KM>::smem));                                                             \
+  gemm_nn_small_kernel<KM><<<grid, 256, NnSmall<KM>::smem, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, \
+                                                                 Z, ld_z, per)
+    if (K1 <= 64) {
+      MC_NN_SMALL(64);
+    } else if (K1 <= 128) {
+      MC_NN_SMALL(128);
+    } else {
+      MC_NN_SMALL(256);
+    }
+#undef MC_NN_SMALL
     MC_CHECK_LAUNCH();
     return;
   }

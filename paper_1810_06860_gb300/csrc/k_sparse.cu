@@ -126,6 +126,126 @@ __global__ void csc_scatter_kernel(int64_t m, int64_t n, int nblk, const int *__
   }
 }
 
+// ------------------------------------------------------------- COO ingest ---
+// Entries in any order: key = row * n + col (checked), a stable LSD radix
+// sort of (key, original index) with 8-bit digits, then the CSR arrays.
+constexpr int RS_THREADS = 256, RS_TILE = 4096;
+
+__global__ void coo_keys_kernel(int64_t nnz, int64_t m, int64_t n, const int64_t *__restrict__ rows,
+                                const int *__restrict__ cols, const float *__restrict__ vals,
+                                unsigned long long *__restrict__ keys, int *__restrict__ idx, int *__restrict__ flags) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = rows[e];
+    const int c = cols[e];
+    if (r < 0 || r >= m || c < 0 || c >= n) {
+      atomicOr(flags + 1, 1);
+      keys[e] = 0ull;
+    } else {
+      keys[e] = (unsigned long long)r * (unsigned long long)n + (unsigned long long)c;
+    }
+    if (!isfinite(vals[e])) atomicOr(flags + 2, 1);
+    idx[e] = static_cast<int>(e);
+  }
+}
+
+// digit counts per tile: hist[d * ntile + tile]
+__global__ void __launch_bounds__(RS_THREADS)
+radix_hist_kernel(int64_t nnz, const unsigned long long *__restrict__ keys, int shift, int *__restrict__ hist) {
+  __shared__ int cnt[256];
+  const int ntile = gridDim.x;
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t b0 = (int64_t)blockIdx.x * RS_TILE, b1 = min(nnz, b0 + RS_TILE);
+  for (int64_t e = b0 + threadIdx.x; e < b1; e += RS_THREADS) atomicAdd(&cnt[(keys[e] >> shift) & 255ull], 1);
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntile + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Scatter in order: within a tile, chunks of 256 entries; a warp ranks equal
+// digits with a match mask, warps add the counts of the warps before them,
+// and a running base per digit carries over from chunk to chunk (stable).
+__global__ void __launch_bounds__(RS_THREADS)
+radix_scatter_kernel(int64_t nnz, const unsigned long long *__restrict__ kin, const int *__restrict__ vin, int shift,
+                     const int *__restrict__ offs, unsigned long long *__restrict__ kout, int *__restrict__ vout) {
+  constexpr int NWP = RS_THREADS / 32;
+  __shared__ int base[256];
+  __shared__ int wc[NWP][256];
+  const int ntile = gridDim.x, tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  base[tid] = offs[(int64_t)tid * ntile + blockIdx.x];
+  const int64_t b0 = (int64_t)blockIdx.x * RS_TILE, b1 = min(nnz, b0 + RS_TILE);
+  for (int64_t c0 = b0; c0 < b1; c0 += RS_THREADS) {
+    for (int q = tid; q < NWP * 256; q += RS_THREADS) (&wc[0][0])[q] = 0;
+    __syncthreads();
+    const int64_t e = c0 + tid;
+    const bool act = e < b1;
+    unsigned long long key = act ? kin[e] : 0ull;
+    const int dg = static_cast<int>((key >> shift) & 255ull);
+    const unsigned amask = __ballot_sync(0xffffffffu, act);
+    int wrank = 0;
+    if (act) {
+      const unsigned peers = __match_any_sync(amask, dg);
+      wrank = __popc(peers & ((1u << lane) - 1u));
+      if (wrank == 0) wc[wid][dg] = __popc(peers);
+    }
+    __syncthreads();
+    if (act) {
+      int pos = base[dg] + wrank;
+      for (int w = 0; w < wid; ++w) pos += wc[w][dg];
+      kout[pos] = key;
+      vout[pos] = vin[e];
+    }
+    __syncthreads();
+    int tot = 0;
+    for (int w = 0; w < NWP; ++w) tot += wc[w][tid];
+    base[tid] += tot;
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of a long int array by one block, chunk after chunk.
+__global__ void scan_long_kernel(int64_t count, const int *__restrict__ in, int *__restrict__ out) {
+  __shared__ int sh[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b = 0; b < count; b += blockDim.x) {
+    const int64_t i = b + threadIdx.x;
+    const int v = i < count ? in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+      const int t = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < count) out[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += sh[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// CSR from the sorted keys: columns, values (gathered by original index),
+// duplicates flagged, row counts for the row pointer.
+__global__ void coo_csr_kernel(int64_t nnz, int64_t n, const unsigned long long *__restrict__ keys,
+                               const int *__restrict__ idx, const float *__restrict__ vals, int *__restrict__ col,
+                               float *__restrict__ val, int *__restrict__ rowcnt, int *__restrict__ flags) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = keys[e];
+    if (e > 0 && keys[e - 1] == k) atomicOr(flags + 1, 2);
+    const int64_t r = static_cast<int64_t>(k / (unsigned long long)n);
+    col[e] = static_cast<int>(k - (unsigned long long)r * (unsigned long long)n);
+    val[e] = vals[idx[e]];
+    atomicAdd(rowcnt + r, 1);
+  }
+}
+
+__global__ void widen_rowptr_kernel(int64_t m, const int *__restrict__ rp32, int64_t *__restrict__ rp64) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= m; i += (int64_t)gridDim.x * blockDim.x)
+    rp64[i] = rp32[i];
+}
+
 // --------------------------------------------------------------- products ---
 // G lane groups per warp (a group owns one gathered panel row at a time), U
 // gathers in flight per group.  Group g takes the segment's entries g, g + G,
@@ -394,6 +514,51 @@ void validate_csr(cudaStream_t st, int64_t m, int64_t n, const int *row_ptr, con
   MC_CHECK_LAUNCH();
 }
 
+void coo_to_csr(cudaStream_t st, Alloc &a, int64_t m, int64_t n, int64_t nnz, const int64_t *rows, const int *cols,
+                const float *vals, int64_t *row_ptr, int *col, float *val, int *flags) {
+  if (nnz <= 0) {
+    MC_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t) * (m + 1), st));
+    return;
+  }
+  const int64_t ntile = (nnz + RS_TILE - 1) / RS_TILE;
+  DBuf k0, k1, v0, v1, hist, offs, cnt, rp32;
+  k0.reserve(a, sizeof(unsigned long long) * nnz);
+  k1.reserve(a, sizeof(unsigned long long) * nnz);
+  v0.reserve(a, sizeof(int) * nnz);
+  v1.reserve(a, sizeof(int) * nnz);
+  hist.reserve(a, sizeof(int) * 256 * ntile);
+  offs.reserve(a, sizeof(int) * (256 * ntile + 1));
+  coo_keys_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, m, n, rows, cols, vals, k0.as<unsigned long long>(),
+                                                      v0.as<int>(), flags);
+  MC_CHECK_LAUNCH();
+  const unsigned long long maxkey = (unsigned long long)m * (unsigned long long)n - 1ull;
+  int bits = 0;
+  while (bits < 64 && (maxkey >> bits) != 0ull) ++bits;
+  unsigned long long *kin = k0.as<unsigned long long>(), *kout = k1.as<unsigned long long>();
+  int *vin = v0.as<int>(), *vout = v1.as<int>();
+  for (int shift = 0; shift < bits; shift += 8) {
+    radix_hist_kernel<<<(unsigned)ntile, RS_THREADS, 0, st>>>(nnz, kin, shift, hist.as<int>());
+    MC_CHECK_LAUNCH();
+    scan_long_kernel<<<1, 1024, 0, st>>>(256 * ntile, hist.as<int>(), offs.as<int>());
+    MC_CHECK_LAUNCH();
+    radix_scatter_kernel<<<(unsigned)ntile, RS_THREADS, 0, st>>>(nnz, kin, vin, shift, offs.as<int>(), kout, vout);
+    MC_CHECK_LAUNCH();
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  cnt.reserve(a, sizeof(int) * (m + 1));
+  rp32.reserve(a, sizeof(int) * (m + 1));
+  MC_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (m + 1), st));
+  coo_csr_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, n, kin, vin, vals, col, val, cnt.as<int>(), flags);
+  MC_CHECK_LAUNCH();
+  exclusive_scan_kernel<<<1, 1024, 0, st>>>(m, cnt.as<int>(), rp32.as<int>());
+  MC_CHECK_LAUNCH();
+  widen_rowptr_kernel<<<grid_for(m + 1, 256), 256, 0, st>>>(m, rp32.as<int>(), row_ptr);
+  MC_CHECK_LAUNCH();
+  MC_CUDA(cudaStreamSynchronize(st));
+  for (DBuf *b : {&k0, &k1, &v0, &v1, &hist, &offs, &cnt, &rp32}) b->release(a);
+}
+
 void convert_rowptr(cudaStream_t st, int64_t m, int64_t nnz, const int64_t *rp64, int *rp32, int *flags) {
   rowptr_check_kernel<<<grid_for(m + 1, 256), 256, 0, st>>>(m, nnz, rp64, rp32, flags);
   MC_CHECK_LAUNCH();
@@ -475,8 +640,6 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
 }
 
 namespace {
-// default gathers in flight for a lane-group count
-int default_u(int G) { return G >= 8 ? 1 : (G >= 2 ? 2 : 4); }
 int lane_groups(int K4) { return K4 <= 2 ? 16 : (K4 <= 4 ? 8 : (K4 <= 8 ? 4 : (K4 <= 16 ? 2 : 1))); }
 int default_chunk(int64_t rows_in) {
   // column chunks of at most 128, narrower when the panel slice would not stay

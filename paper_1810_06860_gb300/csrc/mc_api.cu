@@ -1010,6 +1010,62 @@ mc_status mc_create(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int
   return MC_OK;
 }
 
+mc_status mc_create_coo(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int64_t *rows, const int32_t *cols,
+                        const float *vals, void *stream, const mc_allocator *alloc) {
+  if (!out) return MC_EINVAL;
+  *out = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool own = false;
+  Alloc a;
+  DBuf r_d, c_d, v_d, rp, ci, va, fl;
+  mc_status res = guarded([&]() -> mc_status {
+    MC_REQUIRE(m >= 1 && n >= 1, "m and n must be >= 1");
+    MC_REQUIRE(m < (int64_t(1) << 31) && n < (int64_t(1) << 31), "m and n must be < 2^31");
+    MC_REQUIRE(nnz >= 0 && nnz < (int64_t(1) << 31), "nnz must be in [0, 2^31)");
+    MC_REQUIRE(nnz == 0 || (rows && cols && vals), "null input array");
+    if (!st) {
+      MC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      own = true;
+    }
+    if (alloc) {
+      MC_REQUIRE(alloc->alloc && alloc->free, "allocator hook needs alloc and free");
+      a.hook = *alloc;
+      a.has_hook = true;
+    }
+    a.stream = st;
+    const size_t nz = (size_t)std::max<int64_t>(nnz, 1);
+    r_d.reserve(a, sizeof(int64_t) * nz);
+    c_d.reserve(a, sizeof(int) * nz);
+    v_d.reserve(a, sizeof(float) * nz);
+    rp.reserve(a, sizeof(int64_t) * (m + 1));
+    ci.reserve(a, sizeof(int) * nz);
+    va.reserve(a, sizeof(float) * nz);
+    fl.reserve(a, sizeof(int) * 4);
+    MC_CUDA(cudaMemsetAsync(fl.p, 0, sizeof(int) * 4, st));
+    copy_in(st, r_d.p, rows, sizeof(int64_t) * nnz);
+    copy_in(st, c_d.p, cols, sizeof(int) * nnz);
+    copy_in(st, v_d.p, vals, sizeof(float) * nnz);
+    coo_to_csr(st, a, m, n, nnz, r_d.as<int64_t>(), c_d.as<int>(), v_d.as<float>(), rp.as<int64_t>(), ci.as<int>(),
+               va.as<float>(), fl.as<int>());
+    int h_fl[4] = {0, 0, 0, 0};
+    MC_CUDA(cudaMemcpyAsync(h_fl, fl.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    MC_CUDA(cudaStreamSynchronize(st));
+    MC_REQUIRE(!(h_fl[1] & 1), "row or column index out of range");
+    MC_REQUIRE(!(h_fl[1] & 2), "repeated (row, column) entry");
+    MC_REQUIRE(h_fl[2] == 0, "values must be finite");
+    return MC_OK;
+  });
+  if (res == MC_OK)
+    res = mc_create(out, m, n, nnz, rp.as<int64_t>(), ci.as<int>(), va.as<float>(), own ? nullptr : stream, alloc);
+  if (st) cudaStreamSynchronize(st);
+  for (DBuf *b : {&r_d, &c_d, &v_d, &rp, &ci, &va, &fl}) b->release(a);
+  if (own && st) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  return res;
+}
+
 void mc_destroy(mc_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);

@@ -102,6 +102,11 @@ void convert_rowptr(cudaStream_t st, int64_t m, int64_t nnz, const int64_t *rp64
 // flags: device int[3] (0 ok); host reads back.
 void validate_csr(cudaStream_t st, int64_t m, int64_t n, const int *row_ptr, const int *col,
                   const float *val, int *flags);
+// COO (any order; rows int64, cols int32, device) -> CSR (row_ptr int64,
+// col, val; device).  flags[1] |= 1 for an index out of range, |= 2 for a
+// repeated (row, col); flags[2] |= 1 for a non-finite value.
+void coo_to_csr(cudaStream_t st, Alloc &a, int64_t m, int64_t n, int64_t nnz, const int64_t *rows, const int *cols,
+                const float *vals, int64_t *row_ptr, int *col, float *val, int *flags);
 void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegPlan &plan);
 // out (rows x K, ld_out) = A (CSR ptr/idx/val) * X (cols x K, ld_x).  K, ld_x,
 // ld_out multiples of 4 (padded columns must be zero in X).  partial must hold

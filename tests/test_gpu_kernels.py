@@ -212,3 +212,27 @@ def test_spmm_launch_shapes_bit_identical(mc, tmp_path):
     for other in res[1:]:
         for a, b in zip(res[0], other):
             assert np.array_equal(a, b)
+
+
+def test_coo_ingest_matches_csr(mc):
+    """Coordinates in a shuffled order give the same iterate, bit for bit, as
+    the CSR ingest; a repeated pair and an index out of range are refused."""
+    o = mc_synth.ratings(m=3000, n=900, N=80000, seed=4)
+    rng = np.random.default_rng(1)
+    order = rng.permutation(o.nnz)
+    rows = o.rows[order]
+    cols = o.col[order]
+    vals = o.val[order]
+    with mc.Handle.from_observed(o) as h1, mc.Handle.from_coo(o.m, o.n, rows, cols, vals) as h2:
+        assert np.array_equal(h1.get_values(), h2.get_values())
+        X = rng.standard_normal((o.n, 12)).astype(np.float32)
+        Xt = rng.standard_normal((o.m, 12)).astype(np.float32)
+        assert np.array_equal(h1.spmm(X), h2.spmm(X))
+        assert np.array_equal(h1.spmm(Xt, trans=True), h2.spmm(Xt, trans=True))
+    with pytest.raises(mc.McError) as e:
+        mc.Handle.from_coo(4, 4, np.array([0, 1, 1], np.int64), np.array([2, 3, 3], np.int32), np.ones(3, np.float32))
+    assert e.value.status == 1
+    with pytest.raises(mc.McError):
+        mc.Handle.from_coo(4, 4, np.array([0, 4], np.int64), np.array([2, 3], np.int32), np.ones(2, np.float32))
+    empty = mc.Handle.from_coo(5, 3, np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    empty.close()
