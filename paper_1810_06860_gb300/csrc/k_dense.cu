@@ -109,6 +109,7 @@ gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
   const int i0 = ti * T, j0 = tj * T;
   X += i0;
   Y += j0;
+  same = same && ti == tj;  // one staged panel serves both operands only on a diagonal tile
   extern __shared__ __align__(16) float tns[];
   float *xs = tns;                                          // [STAGES][CH][T]
   float *ys = same ? tns : tns + TNS_STAGES * P::CH * T;    // [STAGES][CH][T]
@@ -956,7 +957,7 @@ size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2) {
 template <int T>
 static void launch_tn_small(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y,
                             int ld_y, bool symg, bool same, float *partial, const TnPlan &pl) {
-  const size_t smem = TnSmall<T>::smem_bytes(same);
+  const size_t smem = TnSmall<T>::smem_bytes(same && pl.tiles_i * pl.tiles_j == 1);
   // the attribute is per kernel and process-wide: always set the largest size
   // any call needs, so concurrent callers on other threads never lower it
   MC_CUDA(cudaFuncSetAttribute(gemm_tn_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
