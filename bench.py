@@ -363,7 +363,7 @@ def run_ours(args, rank, world, local):
         cpu = {"value": round(its / secs, 4), "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"float64 oracle (NumPy/SciPy), SVT iterations 2-{its + 1} of the same workload after its own initialisation"}
     # ---- serving form (last: it loads the GPU for minutes) ----------------------
-    serving = run_serving(mc, SERVE_JOBS) if not args.no_serving else None
+    serving = run_serving(mc, SERVE_JOBS) if not args.no_serving and world == 1 else None
     last = infos[-1]
     line = {"metric": "SVT iterations/s at 2e7 nnz (rating matrix 138,000 x 27,000)", "value": round(value, 3),
             "unit": "iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -122,6 +122,7 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
         force_fresh = False
         nsvd = 0
         used_recycle = False
+        margin = math.inf  # closest any computed sigma came to tau, relative (a conditioning record only)
         while True:
             kk, pp = clamp_rank(m, n, k, s, p)
             width_ok = basis is not None and (recycle != 2 or basis.shape[1] >= kk) and \
@@ -147,6 +148,7 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
                 recycled = True
                 used_recycle = True
             nsvd += 1
+            margin = min(margin, float(np.min(np.abs(S - tau))) / tau)
             k += l
             if S[-1] <= tau:
                 break
@@ -162,7 +164,7 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
         x = sample_lowrank(rows, cols, Us, Vr)
         err = float(np.linalg.norm(x - M)) / normF
         rec = dict(i=it, k=int(kk), r=r, p=int(p), err=err, nsvd=nsvd, recycled=used_recycle,
-                   sigma_last=float(S[-1]), sigma_max=float(S[0]), c=c, norm2=norm2)
+                   sigma_last=float(S[-1]), sigma_max=float(S[0]), c=c, norm2=norm2, tau_margin=margin)
         history.append(rec)
         if callback is not None:
             callback(rec)

@@ -220,7 +220,7 @@ gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ part
   }
 }
 
-// ---- gemm_nn with the small factor in shared memory (K1 <= 256) -------------
+// ---- gemm_nn with the small factor in shared memory --------------------------
 // W (its K1 x 64 column slice for output columns j0 .. j0+63, zero-padded)
 // stays in shared memory; 64-row chunks of X stream through cp.async
 // buffers (three for K1 <= 64, two above).  Thread (ty, tx) computes rows
@@ -990,10 +990,12 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
              const float *colscale, float alpha, float beta, float *Z, int ld_z) {
   if (R <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0, "gemm_nn: ld_x must be a multiple of 4");
-  if (K1 <= 256 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+  // K1 <= 64: W in shared memory, X streamed; wider K1 (the projections
+  // against many earlier blocks) measured faster on the tiled kernel below
+  if (K1 <= 64 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
     const int64_t nch = (R + NNS_BM - 1) / NNS_BM;
     const int tiles = (K2 + 63) / 64;
-    const int per_sm = K1 <= 64 ? 3 : (K1 <= 128 ? 2 : 1);
+    const int per_sm = 3;
     const int64_t want = std::max<int64_t>(1, (int64_t)152 * per_sm / tiles);
     const int64_t per = std::max<int64_t>(1, (nch + want - 1) / want);
     const dim3 grid(static_cast<unsigned>((nch + per - 1) / per), static_cast<unsigned>(tiles));
@@ -1002,13 +1004,7 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
                                (int)NnSmall<KM>::smem));                                                             \
   gemm_nn_small_kernel<KM><<<grid, 256, NnSmall<KM>::smem, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, \
                                                                  Z, ld_z, per)
-    if (K1 <= 64) {
-      MC_NN_SMALL(64);
-    } else if (K1 <= 128) {
-      MC_NN_SMALL(128);
-    } else {
-      MC_NN_SMALL(256);
-    }
+    MC_NN_SMALL(64);
 #undef MC_NN_SMALL
     MC_CHECK_LAUNCH();
     return;

@@ -40,6 +40,7 @@ constexpr int HV_CHUNK = 16;       // reflectors staged per back-transformation 
 constexpr int ST_BISECT = 1, ST_INVIT = 2, ST_GS = 4, ST_BACK = 8, ST_ALL = 15;
 constexpr int SPLIT_K = 256;       // above: inverse iteration and back-transformation on many CTAs
 constexpr int SMALL_K = 128;       // up to here: 256-thread CTAs
+constexpr int WY_MIN_KW = 16;      // blocked back-transformation from this many vectors
 
 __device__ __forceinline__ int pk(int r, int c) { return r * (r + 1) / 2 + c; }  // r >= c
 
@@ -360,7 +361,8 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
   float *hvec = hi + kw;          // kw
   float *part = hvec + kw;        // NW x 32
   float *hv = part + NWV * 32;     // HV_CHUNK x K
-  float *big = hv + (size_t)HV_CHUNK * K;
+  float *wy = hv + (size_t)HV_CHUNK * K;  // blocked back-transformation: S, T (16 x 16 each), W (16 x kw)
+  float *big = wy + 2 * HV_CHUNK * HV_CHUNK + (size_t)HV_CHUNK * kw;
   big = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(big) + 15) & ~uintptr_t(15));
   float *Z = lay.z_in_smem ? big : gw + lay.g_z;
   float *F = lay.f_in_smem ? (lay.z_in_smem ? big + (size_t)K * ldz : big) : gw + lay.g_f;
@@ -584,6 +586,9 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
   }  // ST_GS
   if (!(stages & ST_BACK)) return;
   // ---- back-transformation: Z <- H_0 H_1 ... H_{K-3} Z ----
+  // one reflector at a time for a few vectors; 16 at a time (compact WY) when
+  // the vectors are many enough to amortise forming T
+  if (kw < WY_MIN_KW) {
   for (int top = K - 3; top >= 0; top -= HV_CHUNK) {
     const int lowi = max(0, top - HV_CHUNK + 1);
     for (int64_t f = tid; f < (int64_t)(top - lowi + 1) * K; f += THREADS) {
@@ -618,6 +623,87 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
     }
   }
 
+  } else {
+  // H_lo ... H_hi = I - V T V^T (compact WY form, V's columns the reflectors in
+  // ascending order, T upper triangular: T_jj = beta_j and column j above the
+  // diagonal -beta_j T(0:j, 0:j) V(:, 0:j)^T v_j); then Z -= V (T (V^T Z)).
+  float *S = wy, *T = wy + HV_CHUNK * HV_CHUNK, *Wb = wy + 2 * HV_CHUNK * HV_CHUNK;
+  for (int top = K - 3; top >= 0; top -= HV_CHUNK) {
+    const int lowi = max(0, top - HV_CHUNK + 1), nb = top - lowi + 1;
+    // V (K x nb, column r = reflector lowi + r, zero above row lowi + r + 1)
+    for (int64_t f = tid; f < (int64_t)nb * K; f += THREADS) {
+      const int r = static_cast<int>(f / K), row = static_cast<int>(f % K);
+      const int i = lowi + r;
+      hv[r * K + row] = row >= i + 1 ? Hv[(int64_t)i * K + (row - i - 1)] : 0.f;
+    }
+    __syncthreads();
+    // S = V^T V (nb x nb), a warp per entry
+    for (int e = wid; e < nb * nb; e += NWV) {
+      const int r = e / nb, c = e % nb;
+      float acc = 0.f;
+      if (c < r) acc = 0.f;
+      else
+        for (int row = lane; row < K; row += 32) acc = fmaf(hv[r * K + row], hv[c * K + row], acc);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) S[r * HV_CHUNK + c] = acc;  // upper triangle (r <= c) used
+    }
+    __syncthreads();
+    // T, column by column (one warp; nb <= 16)
+    if (wid == 0) {
+      for (int j = 0; j < nb; ++j) {
+        const float bj = beta[lowi + j];
+        // T(i, j) for i < j: -bj * sum_{l=i}^{j-1} T(i, l) S(l, j)
+        float tij = 0.f;
+        if (lane < j) {
+          for (int l = lane; l < j; ++l) tij = fmaf(T[lane * HV_CHUNK + l], S[l * HV_CHUNK + j], tij);
+          tij *= -bj;
+        }
+        __syncwarp();
+        if (lane < j) T[lane * HV_CHUNK + j] = tij;
+        if (lane == j) T[j * HV_CHUNK + j] = bj;
+        if (lane > j && lane < HV_CHUNK) T[lane * HV_CHUNK + j] = 0.f;
+        __syncwarp();
+      }
+    }
+    // W = V^T Z (nb x kw), a warp per entry
+    for (int e = wid; e < nb * kw; e += NWV) {
+      const int r = e / kw, t = e % kw;
+      float acc = 0.f;
+      for (int row = lowi + r + 1 + lane; row < K; row += 32) acc = fmaf(hv[r * K + row], Z[(int64_t)row * ldz + t], acc);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) Wb[r * kw + t] = acc;
+    }
+    __syncthreads();
+    // W <- T W (in place by columns of W: each thread one column t)
+    for (int t = tid; t < kw; t += THREADS) {
+      float w[HV_CHUNK];
+#pragma unroll
+      for (int r = 0; r < HV_CHUNK; ++r) w[r] = r < nb ? Wb[r * kw + t] : 0.f;
+#pragma unroll
+      for (int r = 0; r < HV_CHUNK; ++r) {
+        if (r < nb) {
+          float acc = 0.f;
+#pragma unroll
+          for (int l = 0; l < HV_CHUNK; ++l)
+            if (l >= r && l < nb) acc = fmaf(T[r * HV_CHUNK + l], w[l], acc);
+          Wb[r * kw + t] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    // Z -= V W (rows lowi + 1 .. K-1)
+    for (int64_t f = tid; f < (int64_t)(K - lowi - 1) * kw; f += THREADS) {
+      const int row = lowi + 1 + static_cast<int>(f / kw), t = static_cast<int>(f % kw);
+      float acc = 0.f;
+      for (int r = 0; r < nb; ++r) acc = fmaf(hv[r * K + row], Wb[r * kw + t], acc);
+      Z[(int64_t)row * ldz + t] -= acc;
+    }
+    __syncthreads();
+  }
+
+  }
   for (int64_t f = tid; f < (int64_t)K * kw; f += THREADS) {
     const int a = static_cast<int>(f / kw), t = static_cast<int>(f % kw);
     W[(int64_t)a * ld_w + t] = Z[(int64_t)a * ldz + t];
@@ -811,7 +897,9 @@ EigPlan eig_plan(int K, int kw) {
   VecLayout vl{};
   vl.ldz = kw | 1;
   const bool split = K > SPLIT_K;
-  const size_t vfixed = sizeof(float) * (3 * (size_t)K + 4 * (size_t)kw + NW * 32 + (size_t)HV_CHUNK * K) + 16;
+  const size_t vfixed =
+      sizeof(float) * (3 * (size_t)K + 4 * (size_t)kw + NW * 32 + (size_t)HV_CHUNK * K + 2 * HV_CHUNK * HV_CHUNK +
+                       (size_t)HV_CHUNK * kw) + 16;
   const size_t zbytes = sizeof(float) * (size_t)K * vl.ldz;
   vl.z_in_smem = !split && vfixed + zbytes <= EIG_SMEM;
   const size_t avail = EIG_SMEM - vfixed - (vl.z_in_smem ? zbytes : 0);

@@ -135,13 +135,39 @@ def test_svt_recycle_q_matches_oracle(mc):
         assert abs(a["err"] - b["err"]) <= 1e-4 * max(1.0, b["err"]), (a, b)
 
 
+# A rank decision (sigma > tau, Alg. 6) whose oracle sigma lies within this
+# relative distance of tau is not fixed by float32 arithmetic: eigSVD (Alg. 3)
+# squares the spectrum and the Krylov basis of rSVD-BKI is ill-conditioned, so
+# trailing Ritz values of a clustered tail carry errors of 1e-4 relative and
+# more.  Trajectories are compared up to the first such decision.
+TAU_MARGIN = 1e-3
+
+
+def _compare_trajectory(hist, ref_hist, min_iters):
+    n = next((j for j, b in enumerate(ref_hist) if b["tau_margin"] < TAU_MARGIN), len(ref_hist))
+    assert n >= min_iters and any(b["recycled"] for b in ref_hist[:n]), n
+    assert len(hist) >= n
+    for a, b in zip(hist[:n], ref_hist[:n]):
+        assert a["r"] == b["r"] and a["k"] == b["k"] and a["recycled"] == int(b["recycled"]), (a, b)
+        assert abs(a["err"] - b["err"]) <= 1e-4 * max(1.0, b["err"]), (a, b)
+
+
 def test_svt_recycle_u_first_iterations(mc):
+    """Image-like 256 x 256 with a clustered tail near tau: the ranks swing
+    between 45 and 175, so recycled U bases of K > 128 columns are exercised."""
     o = mc_synth.smooth_image(256, 256, 10, sigma_px=4.0, frac=0.5, seed=3)
     kw = dict(tau=5 * 256.0, delta=1.2 / 0.5, eps=1e-4, recycle=2, i_reuse=4, q_reuse=3, seed=1)
     ref, hist, _ = _svt_compare(mc, o, kw, i_max=12)
-    for a, b in zip(hist, ref.history):
-        assert a["r"] == b["r"] and a["k"] == b["k"]
-        assert abs(a["err"] - b["err"]) <= 1e-4 * max(1.0, b["err"]), (a, b)
+    _compare_trajectory(hist, ref.history, 5)
+
+
+def test_svt_recycle_u_lowrank(mc):
+    """500 x 500 rank 10: a fresh rSVD every fourth iteration, recycled U
+    bases in between; every decision lies well clear of tau."""
+    o = mc_synth.lowrank_uniform(500, 500, 10, frac=0.2, seed=0)
+    kw = dict(tau=2500.0, delta=6.0, eps=1e-4, recycle=2, i_reuse=4, q_reuse=3, seed=0)
+    ref, hist, _ = _svt_compare(mc, o, kw, i_max=12)
+    _compare_trajectory(hist, ref.history, 12)
 
 
 def test_svt_sample_and_values(mc):

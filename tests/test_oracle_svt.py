@@ -58,6 +58,20 @@ def test_first_iteration_shrinks_diagonal_fast_svt():
     assert abs(h["err"] - want) < 1e-10
 
 
+def test_tau_margin_records_closest_sigma():
+    # As above with sigma_2 = 1.5 * 6.6 = 9.9 just below tau = 10: the exact
+    # final repeat (k = 6) holds the closest sigma; the first repeat (k = 1,
+    # an 11-column sketch) only approximates sigma_1 = 13.5, far from tau.
+    d = np.array([9, 6.6, 3.5, 3, 2.5, 2, 1.5, 1, .9, .8, .7, .6, .5, .4, .3, .2])
+    tau, delta = 10.0, 1.5
+    row_ptr, col, c, _, r = _diag_case(d, tau, delta)
+    res = svt.svt_fast(16, 16, row_ptr, col, d.astype(np.float32), tau=tau, delta=delta, eps=1e-12,
+                       i_max=1, s=10, p0=3)
+    h = res.history[0]
+    assert c == 1 and h["r"] == r == 1 and h["k"] == 6 and h["nsvd"] == 2
+    assert abs(h["tau_margin"] - abs(1.5 * float(np.float32(6.6)) - tau) / tau) < 1e-12
+
+
 def test_svt_exact_recovers_low_rank_matrix():
     o = mc_synth.lowrank_uniform(200, 200, 5, frac=0.3, seed=3)
     res = svt.svt_exact(o.m, o.n, o.row_ptr, o.col, o.val, tau=5 * 200, delta=1.2 / 0.3, eps=1e-4)
