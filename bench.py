@@ -476,6 +476,25 @@ def run_case(args):
         X = torch.randn(138_000, 240, device="cuda")
         for _ in range(3):
             mc.gram(X, tensor_cores=True)
+    elif args.case == "orth":
+        # the Krylov blocks of the SVT step (m = 138,000, k + s = 12, p = 3)
+        # and of rSVD-BKI at k = 50 (60 columns): CUDA-event time per call
+        R, res = 138_000, {}
+        for K, cols in ((12, 0), (12, 12), (12, 24), (12, 36), (60, 0), (60, 180)):
+            Qp = mc.orth_block(torch.randn(R, cols, device="cuda")) if cols else None
+            X0 = torch.randn(R, K, device="cuda")
+            Xs = [X0.clone() for _ in range(max(args.steps, 1) + 3)]
+            for X in Xs[:3]:
+                mc.orth_block(X, Qp)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for X in Xs[3:]:
+                mc.orth_block(X, Qp)
+            e1.record()
+            torch.cuda.synchronize()
+            res[f"K{K}_cols{cols}_us"] = round(1e3 * e0.elapsed_time(e1) / max(args.steps, 1), 1)
+        print(json.dumps(res), flush=True)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "status": "ok"}), flush=True)
 
@@ -516,7 +535,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--case", choices=["spmm", "sddmm", "gram", "serve"], default=None,
+    ap.add_argument("--case", choices=["spmm", "sddmm", "gram", "serve", "orth"], default=None,
                     help="run one small kernel case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3 or args.steps < 1:

@@ -302,6 +302,27 @@ mc_status mc_spmm(mc_handle h, int trans, int k, const float *X, float *out);
  * (K x kw row-major).  The eig() step of eigSVD (Alg. 3).  K <= 1024. */
 mc_status mc_eig_sym(int K, int kw, const float *A, float *lam, float *W);
 
+/* One Krylov block of the orthonormal basis of Alg. 5 (its orth(), built a
+ * block at a time; the span is that of Theorem 2): out (R x K) = an
+ * orthonormal basis of (I - Qp Qp^T) X.  X is projected against the cols
+ * earlier orthonormal columns Qp twice (block classical Gram-Schmidt with
+ * reorthogonalisation), then passed through three CholeskyQR steps (the
+ * first with a shift of 1e-6 trace/K, then two plain ones).  A column whose
+ * squared norm after the projection is at most 1e-10 of its squared norm
+ * before (a dependent direction), or whose Cholesky pivot falls to the
+ * float32 noise floor, is returned as a zero column.  These are the kernels
+ * the rSVD-BKI steps use.
+ *   - Device pointers, row-major: X (R x K, leading dimension ldx),
+ *     Qp (R x cols, ldq), out (R x K, ldo); 16-byte aligned.  X is
+ *     overwritten; out must not overlap X or Qp.
+ *   - K and cols multiples of 4 (zero columns pad a block), K <= 1024;
+ *     ldx, ldq and ldo multiples of 4.  Anything else: MC_EINVAL.
+ *   - Enqueued on stream (a cudaStream_t, NULL for the legacy default
+ *     stream); scratch comes from cudaMallocAsync on that stream; returns
+ *     after the stream has reached the end of the work. */
+mc_status mc_orth_block(int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out, int ldo,
+                        void *stream);
+
 /* Gram matrix G = X^T X (K x K) of a tall X (R x K row-major), the B = A^T A
  * step of eigSVD (Alg. 3).  Host or device. */
 mc_status mc_gram(int64_t R, int K, const float *X, float *G);

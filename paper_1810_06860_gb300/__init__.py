@@ -293,6 +293,28 @@ def gram(X, tensor_cores: bool = False):
     return G
 
 
+def orth_block(X, Qp=None, stream=None):
+    """Orthonormal basis of (I - Qp Qp^T) X for CUDA float32 tensors X (R x K)
+    and Qp (R x cols), K and cols multiples of 4 (mc_orth_block).  X is
+    overwritten; returns a new R x K tensor."""
+    import torch
+
+    lib = load()
+    if X.dtype != torch.float32 or not X.is_cuda or not X.is_contiguous():
+        raise McError(1, "orth_block: X must be a contiguous CUDA float32 tensor")
+    R, K = X.shape
+    out = torch.empty_like(X)
+    cols, pq, ldq = 0, None, 0
+    if Qp is not None and Qp.shape[1] > 0:
+        if Qp.dtype != torch.float32 or not Qp.is_cuda or not Qp.is_contiguous() or Qp.shape[0] != R:
+            raise McError(1, "orth_block: Qp must be a contiguous CUDA float32 tensor with R rows")
+        cols, pq, ldq = Qp.shape[1], C.c_void_p(Qp.data_ptr()), Qp.shape[1]
+    st = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    _check(lib.mc_orth_block(R, K, C.c_void_p(X.data_ptr()), K, pq, ldq, cols, C.c_void_p(out.data_ptr()), K, st),
+           "mc_orth_block")
+    return out
+
+
 class Server:
     """Serving form: whole SVT solves of many jobs on one GPU (mc_server_*).
 

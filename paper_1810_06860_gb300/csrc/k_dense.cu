@@ -685,9 +685,19 @@ __device__ __forceinline__ void on_reduce(const OrthNarrowArgs &a, int count, in
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (ON_THREADS / 32) + (threadIdx.x >> 5), nw = nb * (ON_THREADS / 32);
+  constexpr int BATCH = 8;  // independent loads in flight per lane
   for (int e = gw; e < count; e += nw) {
     float acc = 0.f;
-    for (int b = lane; b < nb; b += 32) acc += a.part[(int64_t)b * stride + e];
+    for (int b0 = lane; b0 < nb; b0 += 32 * BATCH) {
+      float v[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int b = b0 + 32 * u;
+        v[u] = b < nb ? a.part[(int64_t)b * stride + e] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) acc += v[u];  // partials lane, lane + 32, ... in order
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane == 0) dst[e] = acc;
@@ -765,14 +775,19 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
   const int stride = max(CW * KW + KW, KW * KW);  // per-CTA partials of C (+ norms) or of G
   float *fin_C = a.fin, *fin_G = a.fin + stride;
 
-  for (int t = tid; t < nr * ldh; t += ON_THREADS) {
-    const int r = t / ldh, c = t % ldh;
-    Hs[t] = c < K ? a.X[(r0 + r) * a.ldx + c] : 0.f;
+  // rows of X and Qp into shared memory, 16 bytes per copy (K, cols, the
+  // leading dimensions and the bases are multiples of 4 floats); columns
+  // K..ldh and cols..ldq are never read
+  for (int t = tid; t < nr * K4; t += ON_THREADS) {
+    const int r = t / K4, c = t % K4;
+    cp_async16(Hs + r * ldh + 4 * c, a.X + (r0 + r) * a.ldx + 4 * c, 16);
   }
-  for (int t = tid; t < nr * ldq; t += ON_THREADS) {
-    const int r = t / ldq, c = t % ldq;
-    Qs[t] = c < cols ? a.Qp[(r0 + r) * a.ldq + c] : 0.f;
+  for (int t = tid; t < nr * C4; t += ON_THREADS) {
+    const int r = t / C4, c = t % C4;
+    cp_async16(Qs + r * ldq + 4 * c, a.Qp + (r0 + r) * a.ldq + 4 * c, 16);
   }
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
 
   // X -= Qp (Qp^T X), twice; the column norms^2 before the projection (the
@@ -798,7 +813,13 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
     for (int r = tid; r < nr; r += ON_THREADS) {
       float out[KM];
 #pragma unroll
-      for (int j = 0; j < KM; ++j) out[j] = j < K ? Hs[r * ldh + j] : 0.f;
+      for (int j4 = 0; j4 < KM / 4; ++j4) {
+        const float4 h4 = j4 < K4 ? *reinterpret_cast<const float4 *>(Hs + r * ldh + 4 * j4) : make_float4(0, 0, 0, 0);
+        out[4 * j4 + 0] = h4.x;
+        out[4 * j4 + 1] = h4.y;
+        out[4 * j4 + 2] = h4.z;
+        out[4 * j4 + 3] = h4.w;
+      }
       for (int i4 = 0; i4 < C4; ++i4) {
         const float4 q4 = *reinterpret_cast<const float4 *>(Qs + r * ldq + 4 * i4);
         const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
@@ -818,8 +839,10 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
         }
       }
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
-        if (j < K) Hs[r * ldh + j] = out[j];
+      for (int j4 = 0; j4 < KM / 4; ++j4)
+        if (j4 < K4)
+          *reinterpret_cast<float4 *>(Hs + r * ldh + 4 * j4) =
+              make_float4(out[4 * j4], out[4 * j4 + 1], out[4 * j4 + 2], out[4 * j4 + 3]);
     }
     __syncthreads();
   }
@@ -830,70 +853,104 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
     grid.sync();
     on_reduce(a, KW * KW, stride, fin_G);
     grid.sync();
-    // G (upper triangle reduced; mirrored) -> L L^T and L^{-1}, as chol_inv
-    __shared__ float s_tr, s_max;
-    if (tid == 0) {
-      float tr = 0.f, mx = 0.f;
-      for (int i = 0; i < K; ++i) {
-        tr += fin_G[i * KW + i];
-        mx = fmaxf(mx, fin_G[i * KW + i]);
-      }
-      s_tr = tr;
-      s_max = mx;
-    }
-    for (int i = tid; i < K; i += ON_THREADS)
-      fl[i] = (pass == 0 && a.use_ref && !(fin_G[i * KW + i] > a.ref_tol * refs[i])) ? 0.f : 1.f;
-    __syncthreads();
-    const float shift = (pass == 0 ? a.shift_rel : 0.f) * s_tr / K;
-    const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
+    // G (upper triangle reduced; mirrored) -> L L^T and L^{-1}, as chol_inv:
+    // the lower triangle of G into Ls in one parallel read; then one warp
+    // factors it in registers, lane r holding row r of the trailing matrix
+    // and of the inverse, the pivot column and row broadcast by shuffles
     for (int t = tid; t < K * K; t += ON_THREADS) {
       const int i = t / K, j = t % K;
-      const bool live = fl[i] != 0.f && fl[j] != 0.f;
-      Ls[i * (K + 1) + j] = (j <= i && live) ? fin_G[j * KW + i] + (i == j ? shift : 0.f) : 0.f;
-      Bs[i * (K + 1) + j] = (i == j) ? 1.f : 0.f;
+      Ls[i * (K + 1) + j] = j <= i ? fin_G[j * KW + i] : 0.f;
     }
     __syncthreads();
-    const int wid = tid >> 5, lane = tid & 31;
-    for (int j = 0; j < K; ++j) {
-      const float d = Ls[j * (K + 1) + j];
-      const bool keep = d > drop;
-      const float inv = keep ? rsqrtf(d) : 0.f;
-      for (int i = j + 1 + tid; i < K; i += ON_THREADS) Ls[i * (K + 1) + j] *= inv;
-      for (int c = tid; c <= j; c += ON_THREADS) Bs[j * (K + 1) + c] *= inv;
-      if (tid == 0 && !keep) fl[j] = 0.f;
-      __syncthreads();
-      if (keep)
-        for (int r = j + 1 + wid; r < K; r += ON_THREADS / 32) {
-          const float lr = Ls[r * (K + 1) + j];
-          for (int b = lane; b <= r; b += 32) {
-            if (b <= j) Bs[r * (K + 1) + b] -= lr * Bs[j * (K + 1) + b];
-            else Ls[r * (K + 1) + b] -= lr * Ls[b * (K + 1) + j];
-          }
-        }
-      __syncthreads();
-    }
-    // X <- X R^{-1}, R^{-1}[l][c] = L^{-1}[c][l] (kept l, c only), a thread per row
-    for (int r = tid; r < nr; r += ON_THREADS) {
-      float h[KM];
-#pragma unroll
-      for (int l = 0; l < KM; ++l) h[l] = (l < K && fl[l] != 0.f) ? Hs[r * ldh + l] : 0.f;
+    if (tid < 32) {
+      const int lane = tid;
+      const unsigned full = 0xffffffffu;
+      if (lane < K)
+        fl[lane] = (pass == 0 && a.use_ref && !(Ls[lane * (K + 1) + lane] > a.ref_tol * refs[lane])) ? 0.f : 1.f;
+      float tr = 0.f, mx = 0.f;  // the same order on every lane
+      for (int i = 0; i < K; ++i) {
+        const float g = Ls[i * (K + 1) + i];
+        tr += g;
+        mx = fmaxf(mx, g);
+      }
+      const float shift = (pass == 0 ? a.shift_rel : 0.f) * tr / K;
+      const float drop = fmaxf(1e-30f, 1e-12f * mx) + shift;
+      __syncwarp();
+      const bool live_r = lane < K && fl[lane] != 0.f;
+      float lr_[KM], br_[KM];
 #pragma unroll
       for (int c = 0; c < KM; ++c) {
-        if (c < K) {
-          float acc = 0.f;
-          if (fl[c] != 0.f) {
+        const bool live = live_r && c < K && c <= lane && fl[c] != 0.f;
+        lr_[c] = live ? Ls[lane * (K + 1) + c] + (c == lane ? shift : 0.f) : 0.f;
+        br_[c] = c == lane ? 1.f : 0.f;
+      }
+      __syncwarp();
 #pragma unroll
-            for (int l = 0; l <= c; ++l) acc = fmaf(h[l], Bs[c * (K + 1) + l], acc);
+      for (int j = 0; j < KM; ++j) {
+        if (j >= K) continue;  // uniform; keeps every register index static
+        const float d = __shfl_sync(full, lr_[j], j);
+        const bool keep = d > drop;
+        const float inv = keep ? rsqrtf(d) : 0.f;
+        if (lane > j) lr_[j] *= inv;  // column j of L below the diagonal
+        if (lane == j) {
+#pragma unroll
+          for (int c = 0; c <= j; ++c) br_[c] *= inv;  // row j of L^{-1}
+        }
+        if (lane == 0 && !keep) fl[j] = 0.f;
+        if (keep) {
+          const float lr = lr_[j];
+#pragma unroll
+          for (int b = 0; b < KM; ++b) {
+            if (b <= j) {  // L^{-1}[r][b] -= L[r][j] L^{-1}[j][b]
+              const float bjb = __shfl_sync(full, br_[b], j);
+              if (lane > j) br_[b] -= lr * bjb;
+            } else {       // trailing L[r][b] -= L[r][j] L[b][j], b <= r
+              const float lbj = __shfl_sync(full, lr_[j], b);
+              if (lane > j && b <= lane) lr_[b] -= lr * lbj;
+            }
           }
-          Hs[r * ldh + c] = acc;
         }
       }
+      if (lane < K) {
+#pragma unroll
+        for (int c = 0; c < KM; ++c)
+          if (c < K) Bs[lane * (K + 1) + c] = br_[c];
+      }
+    }
+    __syncthreads();
+    // X <- X R^{-1}, R^{-1}[l][c] = L^{-1}[c][l] (kept l, c only), a thread per row
+    for (int r = tid; r < nr; r += ON_THREADS) {
+      float h[KM], o[KM];
+#pragma unroll
+      for (int l4 = 0; l4 < KM / 4; ++l4) {
+        const float4 h4 = l4 < K4 ? *reinterpret_cast<const float4 *>(Hs + r * ldh + 4 * l4) : make_float4(0, 0, 0, 0);
+        h[4 * l4 + 0] = h4.x;
+        h[4 * l4 + 1] = h4.y;
+        h[4 * l4 + 2] = h4.z;
+        h[4 * l4 + 3] = h4.w;
+      }
+#pragma unroll
+      for (int l = 0; l < KM; ++l) h[l] = (l < K && fl[l] != 0.f) ? h[l] : 0.f;
+#pragma unroll
+      for (int c = 0; c < KM; ++c) {
+        float acc = 0.f;
+        if (c < K && fl[c] != 0.f) {
+#pragma unroll
+          for (int l = 0; l <= c; ++l) acc = fmaf(h[l], Bs[c * (K + 1) + l], acc);
+        }
+        o[c] = acc;
+      }
+#pragma unroll
+      for (int c4 = 0; c4 < KM / 4; ++c4)
+        if (c4 < K4)
+          *reinterpret_cast<float4 *>(Hs + r * ldh + 4 * c4) = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
     }
     __syncthreads();
   }
-  for (int t = tid; t < nr * K; t += ON_THREADS) {
-    const int r = t / K, c = t % K;
-    a.out[(r0 + r) * a.ldo + c] = Hs[r * ldh + c];
+  for (int t = tid; t < nr * K4; t += ON_THREADS) {
+    const int r = t / K4, c = t % K4;
+    *reinterpret_cast<float4 *>(a.out + (r0 + r) * a.ldo + 4 * c) =
+        *reinterpret_cast<const float4 *>(Hs + r * ldh + 4 * c);
   }
 }
 
@@ -1062,6 +1119,11 @@ static size_t on_smem(int64_t rows_per, int K, int cols) {
 bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
                  int ldo, bool use_ref, float shift_rel, float ref_tol, float *scratch) {
   if (K < 1 || K > ON_MAXK || R < 1 || cols < 0) return false;
+  // 16-byte copies of whole rows: widths, leading dimensions and bases in multiples of 4 floats
+  if (K % 4 || cols % 4 || ldx % 4 || ldo % 4 || (cols > 0 && ldq % 4)) return false;
+  if (((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(out) |
+        (cols > 0 ? reinterpret_cast<uintptr_t>(Qp) : 0)) & 15u) != 0)
+    return false;
   if (((cols + 3) / 4) * ((K + 3) / 4) > ON_THREADS) return false;  // one 4 x 4 tile of Qp^T X per thread at most
   int dev = 0, sms = 0, coop = 0;
   MC_CUDA(cudaGetDevice(&dev));

@@ -473,6 +473,22 @@ bool orth_block_fused(mc_handle h, int64_t R, int K, float *X, int ldx, const fl
   return orth_narrow(h->stream, R, K, X, ldx, Qp, ldq, cols, out, ldo, cols > 0, 1e-6f, 1e-10f, scr);
 }
 
+// Steps 3-7 of Alg. 5 for one block: out = an orthonormal basis of
+// (I - Qp Qp^T) X (X clobbered), one cooperative launch for narrow blocks,
+// else norms, two projections and three CholeskyQR passes as separate kernels.
+void orth_step(mc_handle h, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
+               int ldo) {
+  if (orth_block_fused(h, R, K, X, ldx, Qp, ldq, cols, out, ldo)) return;
+  if (cols <= 0) {
+    orth_block(h, R, K, X, ldx, out, ldo);
+    return;
+  }
+  float *ref = fbuf(h, h->lam, (size_t)K + colsumsq_scratch_floats(K));
+  colsumsq(h->stream, R, K, X, ldx, ref, ref + K);
+  project_out(h, R, Qp, ldq, cols, X, K, ldx);
+  orth_block(h, R, K, X, ldx, out, ldo, ref);
+}
+
 void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, const float *warm, int warm_ld,
                 int warm_cols) {
   const bool mixed = h->precision != 0;
@@ -488,17 +504,13 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
   h->bt_ready = 0;
   if (mixed) spmm_Y_bf(h, bf_panel(h, h->Om_bf, h->n, kbp, h->Om.as<float>(), kbp), kbp, H, kbp);
   else spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);  // H_0 = A Omega
-  if (!orth_block_fused(h, h->m, kbp, H, kbp, nullptr, 0, 0, Q, ktp)) orth_block(h, h->m, kbp, H, kbp, Q, ktp);
+  orth_step(h, h->m, kbp, H, kbp, nullptr, 0, 0, Q, ktp);
   for (int i = 1; i <= p; ++i) {
     float *Ti = Bt + (size_t)(i - 1) * kbp;
     spmm_Yt(h, Q + (size_t)(i - 1) * kbp, ktp, kbp, Ti, ktp);  // A^T Q_{i-1}
     if (mixed) spmm_Y_bf(h, bf_panel(h, h->T_bf, h->n, kbp, Ti, ktp), kbp, H, kbp);
     else spmm_Y(h, Ti, ktp, kbp, H, kbp);                     // A (A^T Q_{i-1})
-    if (orth_block_fused(h, h->m, kbp, H, kbp, Q, ktp, i * kbp, Q + (size_t)i * kbp, ktp)) continue;
-    float *ref = fbuf(h, h->lam, (size_t)kbp + colsumsq_scratch_floats(kbp));
-    colsumsq(h->stream, h->m, kbp, H, kbp, ref, ref + kbp);
-    project_out(h, h->m, Q, ktp, i * kbp, H, kbp, kbp);
-    orth_block(h, h->m, kbp, H, kbp, Q + (size_t)i * kbp, ktp, ref);
+    orth_step(h, h->m, kbp, H, kbp, Q, ktp, i * kbp, Q + (size_t)i * kbp, ktp);
   }
   h->Kq = ktp;
   h->q_real = (p + 1) * kb;
@@ -1296,6 +1308,26 @@ mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G) {
     cudaFree(part);
     cudaFree(derr);
     if (herr) fail(MC_ETIMEOUT, "a bounded wait in the tensor-core Gram expired");
+    return MC_OK;
+  });
+}
+
+mc_status mc_orth_block(int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out, int ldo,
+                        void *stream) {
+  if (R < 1 || K < 1 || K > kMaxKt || K % 4 != 0 || cols < 0 || cols % 4 != 0 || !X || !out || ldx < K ||
+      ldo < K || ldx % 4 != 0 || ldo % 4 != 0 || (cols > 0 && (!Qp || ldq < cols || ldq % 4 != 0)))
+    return MC_EINVAL;
+  if (!is_device_ptr(X) || !is_device_ptr(out) || (cols > 0 && !is_device_ptr(Qp))) return MC_EINVAL;
+  if (((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(Qp)) & 15u) != 0)
+    return MC_EINVAL;
+  return guarded([&]() -> mc_status {
+    // a matrix-less handle carries the stream, the allocator and the scratch
+    std::unique_ptr<mc_handle_s, void (*)(mc_handle)> h(new mc_handle_s, mc_destroy);
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->alloc.stream = h->stream;
+    h->m = R;
+    orth_step(h.get(), R, K, X, ldx, Qp, ldq, cols, out, ldo);
+    sync(h.get());
     return MC_OK;
   });
 }
