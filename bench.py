@@ -470,6 +470,13 @@ def run_case(args):
                 prm = mc.params(tau=5.0 * math.sqrt(o.m * o.n), delta=DELTA, eps=1e-4, recycle=1, seed=SEED)
                 for _ in range(3):
                     h.svt_step(prm)
+    elif args.case == "svt":
+        # the timed step alone: the rating workload, warm-up then timed SVT iterations
+        o = load_workload()
+        with mc.Handle(o.m, o.n, o.row_ptr, o.col, o.val) as h:
+            prm = svt_params(mc, o)
+            for _ in range(args.warmup + args.steps):
+                h.svt_step(prm)
     elif args.case == "serve":
         print(json.dumps(run_serving(mc, args.steps)), flush=True)
     elif args.case == "gram":
@@ -535,7 +542,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--case", choices=["spmm", "sddmm", "gram", "serve", "orth"], default=None,
+    ap.add_argument("--case", choices=["spmm", "sddmm", "gram", "serve", "orth", "svt"], default=None,
                     help="run one small kernel case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3 or args.steps < 1:

@@ -233,6 +233,81 @@ struct NnSmall {
   static constexpr size_t smem = sizeof(float) * ((size_t)KM1 * 64 + (size_t)STAGES * NNS_BM * LDX);
 };
 
+// Z (R x K2) = alpha X W diag(colscale) + beta Z for narrow outputs
+// (K2 <= KN <= 16, e.g. the factors U = Q W S of a low-rank estimate): a
+// thread per row, W in shared memory read by broadcast, the row of X read
+// with 16-byte loads; sums over k in ascending order as in the tiled kernels.
+template <int KN>
+__global__ void __launch_bounds__(256)
+gemm_nn_narrow_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ W,
+                      int ld_w, const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z,
+                      int ld_z) {
+  extern __shared__ __align__(16) float wn[];  // K1 x KN, zero beyond K2
+  for (int e = threadIdx.x; e < K1 * KN; e += blockDim.x) {
+    const int k = e / KN, j = e % KN;
+    wn[e] = j < K2 ? W[(int64_t)k * ld_w + j] : 0.f;
+  }
+  float sc[KN];
+#pragma unroll
+  for (int j = 0; j < KN; ++j) sc[j] = j < K2 ? alpha * (colscale ? colscale[j] : 1.0f) : 0.f;
+  __syncthreads();
+  const bool vec_in = ld_x % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+  const bool vec_out = K2 == KN && ld_z % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15u) == 0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+    const float *xr = X + r * ld_x;
+    float acc[KN];
+#pragma unroll
+    for (int j = 0; j < KN; ++j) acc[j] = 0.f;
+    int k = 0;
+    if (vec_in)
+      for (; k + 4 <= K1; k += 4) {
+        const float4 x4 = __ldg(reinterpret_cast<const float4 *>(xr + k));
+        const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float4 *wr = reinterpret_cast<const float4 *>(wn + (k + t) * KN);
+#pragma unroll
+          for (int j4 = 0; j4 < KN / 4; ++j4) {
+            const float4 w4 = wr[j4];
+            acc[4 * j4 + 0] = fmaf(xv[t], w4.x, acc[4 * j4 + 0]);
+            acc[4 * j4 + 1] = fmaf(xv[t], w4.y, acc[4 * j4 + 1]);
+            acc[4 * j4 + 2] = fmaf(xv[t], w4.z, acc[4 * j4 + 2]);
+            acc[4 * j4 + 3] = fmaf(xv[t], w4.w, acc[4 * j4 + 3]);
+          }
+        }
+      }
+    for (; k < K1; ++k) {
+      const float xv = __ldg(xr + k);
+#pragma unroll
+      for (int j = 0; j < KN; ++j) acc[j] = fmaf(xv, wn[k * KN + j], acc[j]);
+    }
+    float *z = Z + r * ld_z;
+    if (vec_out) {
+#pragma unroll
+      for (int j4 = 0; j4 < KN / 4; ++j4) {
+        float4 o = make_float4(acc[4 * j4] * sc[4 * j4], acc[4 * j4 + 1] * sc[4 * j4 + 1],
+                               acc[4 * j4 + 2] * sc[4 * j4 + 2], acc[4 * j4 + 3] * sc[4 * j4 + 3]);
+        if (beta != 0.f) {
+          const float4 pz = *reinterpret_cast<const float4 *>(z + 4 * j4);
+          o.x += beta * pz.x;
+          o.y += beta * pz.y;
+          o.z += beta * pz.z;
+          o.w += beta * pz.w;
+        }
+        *reinterpret_cast<float4 *>(z + 4 * j4) = o;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < KN; ++j) {
+        if (j >= K2) continue;
+        float o = acc[j] * sc[j];
+        if (beta != 0.f) o += beta * z[j];
+        z[j] = o;
+      }
+    }
+  }
+}
+
 template <int KM1>
 __global__ void __launch_bounds__(256)
 gemm_nn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ W,
@@ -1047,6 +1122,23 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
              const float *colscale, float alpha, float beta, float *Z, int ld_z) {
   if (R <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0, "gemm_nn: ld_x must be a multiple of 4");
+  // narrow outputs: a thread per row (the 64-column tiles would leave most threads idle)
+  if (K2 <= 16 && K1 <= 1024) {
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, 152 * 8)));
+#define MC_NN_NARROW(KN)                                                                                              \
+  gemm_nn_narrow_kernel<KN><<<grid, 256, sizeof(float) * (size_t)K1 * KN, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, \
+                                                                              alpha, beta, Z, ld_z)
+    if (K2 <= 4) MC_NN_NARROW(4);
+    else if (K2 <= 8) MC_NN_NARROW(8);
+    else {
+      MC_CUDA(cudaFuncSetAttribute(gemm_nn_narrow_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(float) * 1024 * 16)));
+      MC_NN_NARROW(16);
+    }
+#undef MC_NN_NARROW
+    MC_CHECK_LAUNCH();
+    return;
+  }
   // K1 <= 64: W in shared memory, X streamed; wider K1 (the projections
   // against many earlier blocks) measured faster on the tiled kernel below
   if (K1 <= 64 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {

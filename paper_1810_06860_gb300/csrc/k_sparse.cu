@@ -376,19 +376,47 @@ __global__ void to_bf16_kernel(int64_t rows, int cols, const float *__restrict__
   }
 }
 
-// A thread per (split row, column): the row's segment partials added in
-// segment order (the same order for every launch shape).
+// A warp per (split row, group of 4 columns): lane l adds the row's segment
+// partials l, l + 32, ... (four loads in flight), and the 32 lane sums meet
+// in a fixed shuffle tree.  The order is the same for every launch shape; a
+// column with hundreds of segments (the popular columns of rating data)
+// takes a few load latencies instead of one per segment.
 __global__ void spmm_fixup_kernel(int64_t nsplit, const int *__restrict__ split_row,
                                   const int *__restrict__ split_slot, const float *__restrict__ partial, int K,
                                   float *__restrict__ out, int ld_out) {
-  const int64_t total = nsplit * K;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / K;
-    const int c = static_cast<int>(t - i * K);
+  const int K4 = K / 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = nsplit * K4;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nw; w += wstride) {
+    const int64_t i = w / K4;
+    const int c4 = static_cast<int>(w - i * K4);
     const int s0 = split_slot[i], s1 = split_slot[i + 1];
-    float acc = 0.f;
-    for (int sg = s0; sg < s1; ++sg) acc += partial[(int64_t)sg * K + c];
-    out[(int64_t)split_row[i] * ld_out + c] = acc;
+    const float *src = partial + 4 * c4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int b = s0 + lane; b < s1; b += 4 * 32) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int sg = b + 32 * u;
+        v[u] = sg < s1 ? *reinterpret_cast<const float4 *>(src + (int64_t)sg * K) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc.x += v[u].x;
+        acc.y += v[u].y;
+        acc.z += v[u].z;
+        acc.w += v[u].w;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+      acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+      acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
+    }
+    if (lane == 0) *reinterpret_cast<float4 *>(out + (int64_t)split_row[i] * ld_out + 4 * c4) = acc;
   }
 }
 
@@ -704,7 +732,7 @@ void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val
 #undef MC_SEG_ARGS
     MC_CHECK_LAUNCH();
     if (plan.nsplit > 0) {
-      spmm_fixup_kernel<<<grid_for(plan.nsplit * kc, 256), 256, 0, st>>>(
+      spmm_fixup_kernel<<<grid_for(plan.nsplit * (kc / 4) * 32, 256), 256, 0, st>>>(
           plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, kc, out + c0, ld_out);
       MC_CHECK_LAUNCH();
     }
@@ -729,7 +757,7 @@ void spmm_bf16(cudaStream_t st, const SegPlan &plan, const int *idx, const float
 #undef MC_BF_ARGS
   MC_CHECK_LAUNCH();
   if (plan.nsplit > 0) {
-    spmm_fixup_kernel<<<grid_for(plan.nsplit * K, 256), 256, 0, st>>>(
+    spmm_fixup_kernel<<<grid_for(plan.nsplit * (K / 4) * 32, 256), 256, 0, st>>>(
         plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, K, out, ld_out);
     MC_CHECK_LAUNCH();
   }

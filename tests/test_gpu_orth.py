@@ -99,3 +99,21 @@ def test_orth_block_rejects_bad_shapes(mc):
     Q = torch.zeros((100, 6), device="cuda")
     with pytest.raises(mc.McError):
         mc.orth_block(X, Q)
+
+
+@pytest.mark.skipif(__import__("os").environ.get("MC_ORTH_FUSED") == "0", reason="already the separate kernels")
+def test_orth_block_separate_kernels(mc):
+    """The same cases with the one-launch path switched off (MC_ORTH_FUSED=0):
+    narrow blocks then go through the separate Gram, Cholesky and panel
+    product kernels (the narrow-output panel product with beta = 1 in the
+    projection)."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MC_ORTH_FUSED="0")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(root, "tests", "test_gpu_orth.py"), "-q", "-x",
+                        "-p", "no:cacheprovider", "-k", "matches_qr or dependent"], env=env, cwd=root,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
