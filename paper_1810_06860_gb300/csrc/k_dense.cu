@@ -734,14 +734,17 @@ __global__ void select_cols_kernel(int K, const float *__restrict__ W, int ld_w,
 // One cooperative kernel for a whole Krylov block of width K <= 32 (the
 // narrow blocks of the SVT iteration): optional column norms before the
 // projection (the dependence test), two projections against the earlier
-// blocks Qp (X -= Qp (Qp^T X)), then three CholeskyQR passes (shifted, plain,
-// plain), exactly the sequence of the separate kernels.  Each CTA keeps its
+// blocks Qp (X -= Qp (Qp^T X)), then CholeskyQR passes: a shifted one, a
+// plain one, and a third unless the shifted pass already left the block
+// orthonormal to within 1e-2 (the separate kernels always run all three).
+// Each CTA keeps its
 // rows of X and Qp in shared memory for the whole sequence; every reduction
 // over rows is per-CTA partials, a grid barrier, a fixed-order sum split
 // across the CTAs, and a second barrier.  The K x K Cholesky-inverse is
 // repeated by every CTA (it is tiny), so its result needs no barrier.
 constexpr int ON_THREADS = 256;
 constexpr int ON_MAXK = 32;
+constexpr float ON_SKIP3 = 1e-2f;  // max |G - I| of the second pass that makes the third redundant
 
 struct OrthNarrowArgs {
   int64_t R, rows_per;
@@ -922,7 +925,14 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
     __syncthreads();
   }
 
-  // three CholeskyQR passes: X <- X R^{-1} with X^T X + shift I = R^T R
+  // CholeskyQR passes: X <- X R^{-1} with X^T X + shift I = R^T R, the first
+  // shifted.  The third is skipped when the second pass's Gram is within
+  // ON_SKIP3 of the identity on its live columns: its input then has a
+  // condition number near 1, one pass leaves O(u) orthogonality (the
+  // CholeskyQR2 bound) and a third would change nothing that matters.  Every
+  // CTA reduces the same Gram in the same order, so all take the same branch.
+  __shared__ int s_skip3;
+  if (tid == 0) s_skip3 = 0;
   for (int pass = 0; pass < 3; ++pass) {
     on_tile_products(Hs, ldh, K4, Hs, ldh, K4, nr, true, red, a.part + (int64_t)blockIdx.x * stride);
     grid.sync();
@@ -950,13 +960,26 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
       }
       const float shift = (pass == 0 ? a.shift_rel : 0.f) * tr / K;
       const float drop = fmaxf(1e-30f, 1e-12f * mx) + shift;
+      if (pass == 1) {
+        // largest |G - I| over live columns (zero columns, dropped before, excluded)
+        float dev = 0.f;
+        if (lane < K && Ls[lane * (K + 1) + lane] > 0.5f)
+          for (int c = 0; c <= lane; ++c)
+            if (Ls[c * (K + 1) + c] > 0.5f) dev = fmaxf(dev, fabsf(Ls[lane * (K + 1) + c] - (c == lane ? 1.f : 0.f)));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dev = fmaxf(dev, __shfl_xor_sync(full, dev, off));
+        if (lane == 0) s_skip3 = dev <= ON_SKIP3;
+      }
       __syncwarp();
-      const bool live_r = lane < K && fl[lane] != 0.f;
+      const int rl = min(lane, K - 1);  // clamped indices: every load is in bounds, all issue at once
+      const bool live_r = lane < K && fl[rl] != 0.f;
       float lr_[KM], br_[KM];
 #pragma unroll
       for (int c = 0; c < KM; ++c) {
-        const bool live = live_r && c < K && c <= lane && fl[c] != 0.f;
-        lr_[c] = live ? Ls[lane * (K + 1) + c] + (c == lane ? shift : 0.f) : 0.f;
+        const int cl = min(c, K - 1);
+        const float g = Ls[rl * (K + 1) + cl];
+        const bool live = live_r && c < K && c <= lane && fl[cl] != 0.f;
+        lr_[c] = live ? g + (c == lane ? shift : 0.f) : 0.f;
         br_[c] = c == lane ? 1.f : 0.f;
       }
       __syncwarp();
@@ -1021,6 +1044,7 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
           *reinterpret_cast<float4 *>(Hs + r * ldh + 4 * c4) = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
     }
     __syncthreads();
+    if (pass == 1 && s_skip3) break;
   }
   for (int t = tid; t < nr * K4; t += ON_THREADS) {
     const int r = t / K4, c = t % K4;
