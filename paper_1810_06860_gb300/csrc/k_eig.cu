@@ -68,6 +68,97 @@ __device__ __forceinline__ float block_sum_n(float v, float *red) {
   return t;
 }
 
+// Householder tridiagonalisation for K <= 64: a thread per row of the full
+// symmetric matrix, kept in shared memory with row stride 65 (a column read
+// by the 32 threads of a warp hits 32 banks), two warps.  Each step forms
+// the reflector of the column below the subdiagonal, p = beta A' v as one
+// dot product per row, c = beta (v . p) / 2, w = p - c v, and
+// A' -= v w^T + w v^T a row per thread: a handful of barriers per step
+// instead of the warp-per-row reductions of the wider kernel.  Outputs
+// (d, e, beta, reflectors in Hv) as eig_tridiag_kernel.
+constexpr int TS_K = 64, TS_LD = TS_K + 1, TS_THREADS = 64;
+
+__device__ __forceinline__ float ts_sum(float v, float (*red)[2], int &rb) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[rb][threadIdx.x >> 5] = v;
+  __syncthreads();
+  const float t = red[rb][0] + red[rb][1];
+  rb ^= 1;
+  return t;
+}
+
+__global__ void __launch_bounds__(TS_THREADS, 1)
+eig_tridiag_small_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d,
+                         float *__restrict__ g_e, float *__restrict__ g_beta, float *__restrict__ Hv) {
+  __shared__ float S[TS_K * TS_LD];
+  __shared__ float vs[TS_K], ws[TS_K];
+  __shared__ float red[2][2], s_amax[2];
+  const int t = threadIdx.x;
+  float amax = 0.f;
+  for (int e = t; e < K * K; e += TS_THREADS) {
+    const int r = e / K, c = e % K;
+    const float x = r >= c ? A[(int64_t)r * lda + c] : A[(int64_t)c * lda + r];  // lower triangle read
+    S[r * TS_LD + c] = x;
+    amax = fmaxf(amax, fabsf(x));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+  if ((t & 31) == 0) s_amax[t >> 5] = amax;
+  __syncthreads();
+  amax = fmaxf(s_amax[0], s_amax[1]);
+  // a sub-column below (eps |A|)^2 is rounding residue: not reflected (see eig_tridiag_kernel)
+  const float sig_floor = fmaxf((FLT_EPSILON * amax) * (FLT_EPSILON * amax), 1e-37f);
+  int rb = 0;
+  for (int i = 0; i + 2 < K; ++i) {
+    const int n = K - 1 - i;  // trailing rows and columns i + 1 .. K - 1
+    const bool act = t < n;
+    float *row = S + (i + 1 + t) * TS_LD + (i + 1);  // this thread's row of the trailing block
+    const float x = act ? S[(i + 1 + t) * TS_LD + i] : 0.f;
+    const float sigma = ts_sum(act && t >= 1 ? x * x : 0.f, red, rb);
+    const float x0 = S[(i + 1) * TS_LD + i];
+    float bt = 0.f, alpha = x0, v0 = 0.f;
+    if (sigma > sig_floor) {
+      const float mu = sqrtf(x0 * x0 + sigma);
+      alpha = x0 <= 0.f ? mu : -mu;
+      v0 = x0 - alpha;
+      bt = 2.0f / (v0 * v0 + sigma);
+    }
+    const float vr = t == 0 ? v0 : x;
+    if (t == 0) {
+      g_d[i] = S[i * TS_LD + i];
+      g_e[i] = alpha;
+      g_beta[i] = bt;
+    }
+    if (act) Hv[(int64_t)i * K + t] = vr;
+    if (bt == 0.f) continue;  // uniform: every thread has the same sigma
+    if (act) vs[t] = vr;
+    __syncthreads();
+    float p = 0.f;
+    if (act) {
+      for (int b = 0; b < n; ++b) p = fmaf(row[b], vs[b], p);
+      p *= bt;
+    }
+    const float c = 0.5f * bt * ts_sum(act ? vr * p : 0.f, red, rb);
+    const float w = p - c * vr;
+    if (act) ws[t] = w;
+    __syncthreads();
+    if (act)
+      for (int b = 0; b < n; ++b) row[b] -= vr * ws[b] + w * vs[b];
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (K >= 2) {
+      g_d[K - 2] = S[(K - 2) * TS_LD + (K - 2)];
+      g_e[K - 2] = S[(K - 1) * TS_LD + (K - 2)];
+      g_beta[K - 2] = 0.f;
+    }
+    g_d[K - 1] = S[(K - 1) * TS_LD + (K - 1)];
+    g_e[K - 1] = 0.f;
+    g_beta[K - 1] = 0.f;
+  }
+}
+
 template <int PPR, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
 eig_tridiag_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d, float *__restrict__ g_e,
@@ -430,13 +521,15 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
             cnt += qq < 0.f;
           }
         }
-        float nl = l, nh = h;
-        for (int sidx = 0; sidx < g; ++sidx) {
-          const float xs = __shfl_sync(0xffffffffu, x, (lane / g) * g + sidx);
-          const int cs = __shfl_sync(0xffffffffu, cnt, (lane / g) * g + sidx);
-          if (cs <= target) nl = fmaxf(nl, xs);
-          else nh = fminf(nh, xs);
-        }
+        // the group's points increase with q: the new bracket is the highest
+        // point whose count is <= target and the lowest whose count is above
+        const unsigned gmask = (g == 32 ? 0xffffffffu : ((1u << g) - 1u)) << ((lane / g) * g);
+        const unsigned below = __ballot_sync(0xffffffffu, cnt <= target) & gmask;
+        const unsigned above = __ballot_sync(0xffffffffu, cnt > target) & gmask;
+        const int lb = below ? 31 - __clz(below) : 0, la = above ? __ffs(above) - 1 : 0;
+        const float xb = __shfl_sync(0xffffffffu, x, lb), xa = __shfl_sync(0xffffffffu, x, la);
+        const float nl = below ? fmaxf(l, xb) : l;
+        const float nh = above ? fminf(h, xa) : h;
         __syncthreads();
         if (active && q == 0) {
           lo[t] = nl;
@@ -477,11 +570,11 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
         float l, du2 = 0.f, na, nb;
         if (fabsf(a_cur) >= fabsf(cc)) {
           if (a_cur == 0.f) a_cur = tiny;
-          l = cc / a_cur;
+          l = __fdividef(cc, a_cur);
           na = a_next - l * b_cur;
           nb = b_next;
         } else {
-          l = a_cur / cc;
+          l = __fdividef(a_cur, cc);
           na = b_cur - l * a_next;
           du2 = b_next;
           nb = -l * b_next;
@@ -490,7 +583,9 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
           piv_bits[a >> 5] |= 1u << (a & 31);
         }
         const int o = a * B + tid;
-        fa[o] = 1.0f / (fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
+        // the factors of inverse iteration need no correctly rounded division:
+        // an error of a few ulps only perturbs the shift
+        fa[o] = __fdividef(1.0f, fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
         fb[o] = b_cur;
         fc[o] = du2;
         fl[o] = l;
@@ -499,7 +594,7 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
       }
       {
         const int o = (K - 1) * B + tid;
-        fa[o] = 1.0f / (fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
+        fa[o] = __fdividef(1.0f, fabsf(a_cur) < tiny ? copysignf(tiny, a_cur) : a_cur);
         fb[o] = 0.f;
         fc[o] = 0.f;
       }
@@ -586,9 +681,37 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
   }  // ST_GS
   if (!(stages & ST_BACK)) return;
   // ---- back-transformation: Z <- H_0 H_1 ... H_{K-3} Z ----
-  // one reflector at a time for a few vectors; 16 at a time (compact WY) when
-  // the vectors are many enough to amortise forming T
-  if (kw < WY_MIN_KW) {
+  // up to one vector per warp: each warp applies the staged reflectors to its
+  // vector with warp reductions (no block barrier per reflector); more
+  // vectors: one reflector at a time across the block, and 16 at a time
+  // (compact WY) when the vectors are many enough to amortise forming T
+  if (kw <= NWV) {
+  for (int top = K - 3; top >= 0; top -= HV_CHUNK) {
+    const int lowi = max(0, top - HV_CHUNK + 1);
+    for (int64_t f = tid; f < (int64_t)(top - lowi + 1) * K; f += THREADS) {
+      const int r = static_cast<int>(f / K), a = static_cast<int>(f % K);
+      hv[r * K + a] = Hv[(int64_t)(lowi + r) * K + a];
+    }
+    __syncthreads();
+    if (wid < kw) {
+      const int t = wid;
+      for (int i = top; i >= lowi; --i) {
+        const float bt = beta[i];
+        if (bt == 0.f) continue;
+        const int n = K - 1 - i;
+        const float *v = hv + (i - lowi) * K;
+        float acc = 0.f;
+        for (int a = lane; a < n; a += 32) acc = fmaf(v[a], Z[(int64_t)(i + 1 + a) * ldz + t], acc);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        const float hb = bt * acc;
+        for (int a = lane; a < n; a += 32) Z[(int64_t)(i + 1 + a) * ldz + t] -= v[a] * hb;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  } else if (kw < WY_MIN_KW) {
   for (int top = K - 3; top >= 0; top -= HV_CHUNK) {
     const int lowi = max(0, top - HV_CHUNK + 1);
     for (int64_t f = tid; f < (int64_t)(top - lowi + 1) * K; f += THREADS) {
@@ -955,6 +1078,9 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   }
 #define MC_TRI_ARGS K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta, gw + pl.g_hv, gw + pl.g_p, pl.p_in_smem
   if (done) {
+  } else if (K <= TS_K) {
+    eig_tridiag_small_kernel<<<1, TS_THREADS, 0, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                       gw + pl.g_hv);
   } else if (tc.ppr == 2) {
     MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
     eig_tridiag_kernel<2, 256><<<1, 256, pl.tri_smem, st>>>(MC_TRI_ARGS);

@@ -155,6 +155,12 @@ struct mc_handle_s {
   int q_real = 0;      // real (non-padding) columns of the stored Krylov basis
   int kw = 0;          // eigenpairs in lam/W
   std::vector<float> h_lam;
+  // pinned staging of small host-to-device parameter copies: two slots used
+  // in turn, each with an event marking when its last copy has run
+  float *h_stage[2] = {nullptr, nullptr};
+  size_t h_stage_cap[2] = {0, 0};
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  int stage_next = 0;
   // SVT state
   bool svt_init = false;
   mc_params prm{};
@@ -188,6 +194,28 @@ void copy_out_2d(cudaStream_t st, float *dst, int dst_cols, const float *src, in
 }
 
 void sync(mc_handle h) { MC_CUDA(cudaStreamSynchronize(h->stream)); }
+
+// count floats from host memory to dst (device) on the handle's stream,
+// through a pinned slot: returns without waiting for the copy; a slot is
+// rewritten only after its previous copy has run
+void stage_copy(mc_handle h, float *dst, const float *src, size_t count) {
+  if (count == 0) return;
+  const int s = h->stage_next;
+  h->stage_next ^= 1;
+  if (h->stage_ev[s]) MC_CUDA(cudaEventSynchronize(h->stage_ev[s]));
+  else MC_CUDA(cudaEventCreateWithFlags(&h->stage_ev[s], cudaEventDisableTiming));
+  if (h->h_stage_cap[s] < count) {
+    if (h->h_stage[s]) MC_CUDA(cudaFreeHost(h->h_stage[s]));
+    h->h_stage[s] = nullptr;
+    h->h_stage_cap[s] = 0;
+    const size_t cap = std::max<size_t>(count, 256);
+    MC_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h->h_stage[s]), sizeof(float) * cap));
+    h->h_stage_cap[s] = cap;
+  }
+  std::memcpy(h->h_stage[s], src, sizeof(float) * count);
+  MC_CUDA(cudaMemcpyAsync(dst, h->h_stage[s], sizeof(float) * count, cudaMemcpyHostToDevice, h->stream));
+  MC_CUDA(cudaEventRecord(h->stage_ev[s], h->stream));
+}
 
 float *fbuf(mc_handle h, DBuf &b, size_t count) {
   b.reserve(h->alloc, sizeof(float) * std::max<size_t>(count, 1));
@@ -599,7 +627,7 @@ void form_factors(mc_handle h, const float *Qb, int ldq, int ncols, const std::v
     sc[ldp + j] = (float)sv[j];
   }
   float *dsc = fbuf(h, h->scale, 2 * (size_t)ldp);
-  MC_CUDA(cudaMemcpyAsync(dsc, sc.data(), sizeof(float) * sc.size(), cudaMemcpyHostToDevice, h->stream));
+  stage_copy(h, dsc, sc.data(), sc.size());
   if (U) {
     Scope sc(h, MC_T_GEMM, 4.0 * h->m * (Kq + ldp), 2.0 * h->m * Kq * ldp);
     gemm_nn(h->stream, h->m, Kq, ldp, Qb, ldq, Ws, ldp, dsc, 1.0f, 0.0f, U, ldp);
@@ -608,7 +636,6 @@ void form_factors(mc_handle h, const float *Qb, int ldq, int ncols, const std::v
     Scope sc(h, MC_T_GEMM, 4.0 * h->n * (Kq + ldp), 2.0 * h->n * Kq * ldp);
     gemm_nn(h->stream, h->n, Kq, ldp, h->Bt.as<float>(), Kq, Ws, ldp, dsc + ldp, 1.0f, 0.0f, V, ldp);
   }
-  sync(h);  // keeps sc alive until the copy is done
 }
 
 // Full rSVD into user buffers.
@@ -807,9 +834,8 @@ mc_status svt_step(mc_handle h, mc_iter_info *out) {
       float *Ws = fbuf(h, h->Wsel, (size_t)h->ub_ld * ldp);
       std::vector<float> eye((size_t)h->ub_ld * ldp, 0.f);
       for (int j = 0; j < r; ++j) eye[(size_t)j * ldp + j] = (float)su[j];
-      MC_CUDA(cudaMemcpyAsync(Ws, eye.data(), sizeof(float) * eye.size(), cudaMemcpyHostToDevice, h->stream));
+      stage_copy(h, Ws, eye.data(), eye.size());
       gemm_nn(h->stream, h->m, h->ub_ld, ldp, h->Ub.as<float>(), h->ub_ld, Ws, ldp, nullptr, 1.0f, 0.0f, Us, ldp);
-      sync(h);
     } else {
       form_factors(h, Qb, ldq, r, su, sv, Us, Vr, ldp);
     }
@@ -1091,6 +1117,10 @@ void mc_destroy(mc_handle h) {
     for (DBuf *b : {&pl->seg, &pl->split_row, &pl->split_slot})
       b->release(a);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int q = 0; q < 2; ++q) {
+    if (h->stage_ev[q]) cudaEventDestroy(h->stage_ev[q]);
+    if (h->h_stage[q]) cudaFreeHost(h->h_stage[q]);
+  }
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
