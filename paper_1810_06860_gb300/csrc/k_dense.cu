@@ -749,6 +749,7 @@ constexpr float ON_SKIP3 = 1e-2f;  // max |G - I| of the second pass that makes 
 struct OrthNarrowArgs {
   int64_t R, rows_per;
   int K, cols, ldx, ldq, ldo, use_ref;
+  int q_smem;        // 1: rows of Qp staged in shared memory; 0: read from global (L2)
   float *X;          // R x K (clobbered)
   const float *Qp;   // R x cols
   float *out;        // R x K
@@ -838,13 +839,16 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
   extern __shared__ __align__(16) float onsm[];
   const int K = a.K, cols = a.cols, tid = threadIdx.x;
   const int K4 = (K + 3) / 4, C4 = (cols + 3) / 4, KW = K4 * 4, CW = C4 * 4;
-  const int ldh = on_ld(K), ldq = on_ld(cols);
+  const int ldh = on_ld(K), ldqs = on_ld(cols);
   const int64_t r0 = blockIdx.x * a.rows_per;
   const int64_t r1 = a.R < r0 + a.rows_per ? a.R : r0 + a.rows_per;
   const int nr = r1 > r0 ? static_cast<int>(r1 - r0) : 0;
   float *Hs = onsm;                                   // rows_per x ldh (zero beyond K)
-  float *Qs = Hs + (size_t)a.rows_per * ldh;          // rows_per x ldq (zero beyond cols)
-  float *Ms = Qs + (size_t)a.rows_per * ldq;          // CW x KW (C) or KW x KW (G), and the partial tile
+  float *Qsm = Hs + (size_t)a.rows_per * ldh;         // rows_per x ldqs when staged
+  float *Ms = Qsm + (a.q_smem ? (size_t)a.rows_per * ldqs : 0);  // CW x KW (C) or KW x KW (G)
+  // this CTA's rows of Qp: the staged copy, or the rows in global memory (L2)
+  const float *Qs = a.q_smem ? Qsm : a.Qp + (cols > 0 ? r0 * a.ldq : 0);
+  const int ldq = a.q_smem ? ldqs : a.ldq;
   float *red = Ms + (size_t)max(CW, KW) * KW;         // ON_THREADS x 16
   float *Ls = red + (size_t)ON_THREADS * 16;          // K x (K+1): Cholesky factor
   float *Bs = Ls + (size_t)K * (K + 1);               // K x (K+1): running inverse
@@ -860,10 +864,11 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
     const int r = t / K4, c = t % K4;
     cp_async16(Hs + r * ldh + 4 * c, a.X + (r0 + r) * a.ldx + 4 * c, 16);
   }
-  for (int t = tid; t < nr * C4; t += ON_THREADS) {
-    const int r = t / C4, c = t % C4;
-    cp_async16(Qs + r * ldq + 4 * c, a.Qp + (r0 + r) * a.ldq + 4 * c, 16);
-  }
+  if (a.q_smem)
+    for (int t = tid; t < nr * C4; t += ON_THREADS) {
+      const int r = t / C4, c = t % C4;
+      cp_async16(Qsm + r * ldqs + 4 * c, a.Qp + (r0 + r) * a.ldq + 4 * c, 16);
+    }
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
@@ -1225,9 +1230,9 @@ size_t orth_narrow_scratch_floats(int64_t R, int K, int cols) {
   return (size_t)(nb_max * st + 2 * st + 64);
 }
 
-static size_t on_smem(int64_t rows_per, int K, int cols) {
+static size_t on_smem(int64_t rows_per, int K, int cols, bool q_smem) {
   const int KW = (K + 3) / 4 * 4, CW = (cols + 3) / 4 * 4;
-  return sizeof(float) * ((size_t)rows_per * on_ld(K) + (size_t)rows_per * on_ld(cols) +
+  return sizeof(float) * ((size_t)rows_per * on_ld(K) + (q_smem ? (size_t)rows_per * on_ld(cols) : 0) +
                           (size_t)std::max(CW, KW) * KW + (size_t)ON_THREADS * 16 + 2 * (size_t)K * (K + 1) +
                           2 * (size_t)K);
 }
@@ -1257,10 +1262,15 @@ bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const flo
     const char *v = std::getenv("MC_ORTH_PER_SM");
     return v ? std::max(1, std::min(4, std::atoi(v))) : 4;
   }();
+  // first with the rows of Qp staged too; when they do not fit, Qp is read
+  // from global memory (it stays in L2 between the four passes over it)
+  for (int attempt = 0; attempt < 2; ++attempt)
   for (int per_sm = cap; per_sm >= 1; --per_sm) {
+    const bool q_smem = attempt == 0 && cols > 0;
+    if (attempt == 1 && cols == 0) break;
     const int64_t nb = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (R + 31) / 32));
     const int64_t rows_per = (R + nb - 1) / nb;
-    const size_t smem = on_smem(rows_per, K, cols);
+    const size_t smem = on_smem(rows_per, K, cols, q_smem);
     if (smem > (size_t)220 * 1024 / per_sm) continue;
     int occ = 0;
     MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, ON_THREADS, smem));
@@ -1275,6 +1285,7 @@ bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const flo
     a.ldq = ldq;
     a.ldo = ldo;
     a.use_ref = use_ref ? 1 : 0;
+    a.q_smem = q_smem ? 1 : 0;
     a.X = X;
     a.Qp = Qp;
     a.out = out;

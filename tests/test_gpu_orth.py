@@ -60,9 +60,12 @@ def _check(got, want, Qp, keep, drop):
 
 
 # (R, K, cols, padding columns): narrow blocks take the one-launch path
-# (K <= 32), K = 60 the separate kernels; 1001 and 7 rows leave ragged CTAs
+# (K <= 32), K = 60 the separate kernels; 1001 and 7 rows leave ragged CTAs;
+# at 138,000 x 16 / 48 and 138,000 x 32 / 96 the earlier columns do not fit
+# the CTAs' shared memory and are read from global memory
 @pytest.mark.parametrize("R,K,cols,pad", [(7, 4, 0, 0), (1001, 12, 0, 2), (1001, 12, 36, 0), (138000, 12, 36, 2),
-                                          (50000, 32, 96, 0), (20000, 60, 120, 3), (20000, 60, 0, 0)])
+                                          (50000, 32, 96, 0), (138000, 16, 48, 2), (138000, 32, 96, 0),
+                                          (20000, 60, 120, 3), (20000, 60, 0, 0)])
 def test_orth_block_matches_qr(mc, R, K, cols, pad):
     rng = np.random.default_rng(R + K + cols)
     Qp = _basis(R, cols, rng)
