@@ -195,6 +195,10 @@ typedef struct {
   double flops;
   int64_t launches;
 } mc_timing;
+/* on: 0 off, 1 every class, 2 the two sparse-product classes only (two
+ * events per product instead of two per launch of every class: the lighter
+ * form for a timed region).  Synchronises the handle's stream and resets
+ * the counters. */
 mc_status mc_timing_enable(mc_handle h, int on);
 /* out: MC_T_COUNT entries (host).  Synchronises the handle's stream. */
 mc_status mc_timing_read(mc_handle h, mc_timing *out);

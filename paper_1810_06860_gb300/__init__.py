@@ -242,8 +242,10 @@ class Handle:
         pv, keep = _ptr(val, np.float32)
         _check(self._lib.mc_set_values(self._h, pv), "mc_set_values")
 
-    def timing_enable(self, on: bool = True):
-        _check(self._lib.mc_timing_enable(self._h, 1 if on else 0), "mc_timing_enable")
+    def timing_enable(self, on=True):
+        """True / 1: every kernel class; 2: the sparse products only; False / 0: off."""
+        mode = on if isinstance(on, int) and not isinstance(on, bool) else (1 if on else 0)
+        _check(self._lib.mc_timing_enable(self._h, mode), "mc_timing_enable")
 
     def timing_read(self) -> dict:
         arr = (_native.McTiming * len(_native.TIMING_NAMES))()

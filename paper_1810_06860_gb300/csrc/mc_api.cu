@@ -84,6 +84,7 @@ constexpr int kMaxKt = 1024;  // widest Krylov basis the small eigensolver takes
 // CUDA-event timing of kernel classes on the handle's stream (off by default).
 struct Prof {
   bool on = false;
+  unsigned mask = ~0u;  // kernel classes recorded while on
   struct Rec {
     int cat;
     cudaEvent_t a, b;
@@ -245,7 +246,7 @@ struct Scope {
   double bytes, flops;
   cudaEvent_t a = nullptr;
   Scope(mc_handle h_, int cat_, double bytes_ = 0, double flops_ = 0) : h(h_), cat(cat_), bytes(bytes_), flops(flops_) {
-    if (h->prof.on) {
+    if (h->prof.on && (h->prof.mask >> cat & 1u)) {
       a = h->prof.get();
       MC_CUDA(cudaEventRecord(a, h->stream));
     }
@@ -1260,11 +1261,12 @@ mc_status mc_spmm(mc_handle h, int trans, int k, const float *X, float *out) {
 }
 
 mc_status mc_timing_enable(mc_handle h, int on) {
-  if (!h) return MC_EINVAL;
+  if (!h || on < 0 || on > 2) return MC_EINVAL;
   return guarded([&]() -> mc_status {
     sync(h);
     h->prof.reset();
     h->prof.on = on != 0;
+    h->prof.mask = on == 2 ? (1u << MC_T_SPMM) | (1u << MC_T_SPMM_T) : ~0u;
     return MC_OK;
   });
 }
