@@ -149,9 +149,18 @@ mc_status mc_rsvd_pi(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t c
  * a handle (or the first after mc_svt_reset) also performs step 1: estimates
  * ||P_Phi(M)||_2, sets c and Y^0 = c delta P_Phi(M).  params is read at that
  * first call only.  out (host) receives the iteration record.  Returns MC_OK
- * (also when the tolerance was met: out->converged = 1). */
+ * (also when the tolerance was met: out->converged = 1).  The copy of the
+ * updated Y into CSC order (the values the Y^T X products read) is left
+ * running on a second stream of the handle when the call returns; the
+ * library's own calls wait for it where they need it. */
 mc_status mc_svt_step(mc_handle h, const mc_params *params, mc_iter_info *out);
 mc_status mc_svt_reset(mc_handle h);
+
+/* mc_join: orders the handle's stream after the work the handle left on its
+ * second stream (the copy of Y into CSC order after mc_svt_step), so that an
+ * event recorded on the handle's stream afterwards, or a synchronisation of
+ * it, covers all of the handle's work.  Enqueues a wait only; does not block. */
+mc_status mc_join(mc_handle h);
 
 /* mc_svt_solve: run mc_svt_step until err < eps or i_max.  Returns MC_OK or
  * MC_ENOTCONVERGED (results still available).  out (host, may be NULL)

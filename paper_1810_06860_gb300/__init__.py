@@ -242,6 +242,10 @@ class Handle:
         pv, keep = _ptr(val, np.float32)
         _check(self._lib.mc_set_values(self._h, pv), "mc_set_values")
 
+    def join(self):
+        """Order the handle's stream after its second stream (mc_join)."""
+        _check(self._lib.mc_join(self._h), "mc_join")
+
     def timing_enable(self, on=True):
         """True / 1: every kernel class; 2: the sparse products only; False / 0: off."""
         mode = on if isinstance(on, int) and not isinstance(on, bool) else (1 if on else 0)

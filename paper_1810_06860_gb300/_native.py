@@ -81,6 +81,7 @@ _SIGS = {
     "mc_spmm": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "mc_eig_sym": (C.c_int, [C.c_int, C.c_int, _P, _P, _P]),
     "mc_gram": (C.c_int, [C.c_int64, C.c_int, _P, _P]),
+    "mc_join": (C.c_int, [_P]),
     "mc_orth_block": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, _P, C.c_int, _P]),
     "mc_gram_tc": (C.c_int, [C.c_int64, C.c_int, _P, _P]),
     "mc_gram_noalloc": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int, _P, C.c_int, _P]),

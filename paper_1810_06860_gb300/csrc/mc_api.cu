@@ -139,6 +139,12 @@ struct mc_handle_s {
   int64_t m = 0, n = 0, nnz = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // side stream for the copy of Y into CSC order after an update: it
+  // overlaps the residual read-back, the host decisions and the start of the
+  // next step; readers of the CSC copy wait for ev_yc first
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_yc = nullptr;
+  bool yc_pending = false;
   Alloc alloc;
   // CSR (rix: row of every entry)
   DBuf rp, ci, mval, y, rix;
@@ -244,21 +250,50 @@ struct Scope {
   mc_handle h;
   int cat;
   double bytes, flops;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  Scope(mc_handle h_, int cat_, double bytes_ = 0, double flops_ = 0) : h(h_), cat(cat_), bytes(bytes_), flops(flops_) {
+  Scope(mc_handle h_, int cat_, double bytes_ = 0, double flops_ = 0, cudaStream_t st_ = nullptr)
+      : h(h_), cat(cat_), bytes(bytes_), flops(flops_), st(st_ ? st_ : h_->stream) {
     if (h->prof.on && (h->prof.mask >> cat & 1u)) {
       a = h->prof.get();
-      MC_CUDA(cudaEventRecord(a, h->stream));
+      MC_CUDA(cudaEventRecord(a, st));
     }
   }
   ~Scope() {
     if (a) {
       cudaEvent_t b = h->prof.get();
-      cudaEventRecord(b, h->stream);
+      cudaEventRecord(b, st);
       h->prof.pending.push_back({cat, a, b, bytes, flops});
     }
   }
 };
+
+// The main stream waits for a pending copy of Y into CSC order (before
+// reading the CSC values, or writing Y or the copy).
+void yc_ready(mc_handle h) {
+  if (!h->yc_pending) return;
+  MC_CUDA(cudaStreamWaitEvent(h->stream, h->ev_yc, 0));
+  h->yc_pending = false;
+}
+
+// Copies the updated Y into CSC order on the side stream, after the work
+// already on the main stream.
+void mirror_async(mc_handle h) {
+  yc_ready(h);
+  if (!h->side) {
+    MC_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    MC_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    MC_CUDA(cudaEventCreateWithFlags(&h->ev_yc, cudaEventDisableTiming));
+  }
+  MC_CUDA(cudaEventRecord(h->ev_fork, h->stream));
+  MC_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  {
+    Scope sc(h, MC_T_OTHER, 12.0 * h->nnz, 0, h->side);
+    mirror_values(h->side, h->nnz, h->perm.as<int>(), h->y.as<float>(), h->yc.as<float>());
+  }
+  MC_CUDA(cudaEventRecord(h->ev_yc, h->side));
+  h->yc_pending = true;
+}
 
 double spmm_bytes(int64_t nnz, int64_t rows, int64_t rows_in, int K) {
   return 8.0 * nnz + 4.0 * (rows + 1) + 4.0 * (double)(rows_in + rows) * K;
@@ -379,6 +414,7 @@ void spmm_Y_bf(mc_handle h, const void *X, int K, float *out, int ld_out) {
   spmm_bf16(h->stream, h->plan_r, h->ci.as<int>(), h->y.as<float>(), X, K, K, out, ld_out, h->sp_part.as<float>());
 }
 void spmm_Yt_bf(mc_handle h, const void *X, int K, float *out, int ld_out) {
+  yc_ready(h);
   fbuf(h, h->sp_part, (size_t)h->plan_c.nslot * K);
   Scope sc(h, MC_T_SPMM_T, 8.0 * h->nnz + 4.0 * (h->n + 1) + (2.0 * h->m + 4.0 * h->n) * K, 2.0 * h->nnz * K);
   spmm_bf16(h->stream, h->plan_c, h->ri.as<int>(), h->yc.as<float>(), X, K, K, out, ld_out, h->sp_part.as<float>());
@@ -391,6 +427,7 @@ void *bf_panel(mc_handle h, DBuf &b, int64_t rows, int cols, const float *src, i
 }
 
 void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_out) {
+  yc_ready(h);
   fbuf(h, h->sp_part, (size_t)h->plan_c.nslot * K);
   auto run = [&](const SpmmCfg &c) {
     spmm(h->stream, h->plan_c, h->ri.as<int>(), h->yc.as<float>(), h->m, X, ld_x, K, out, ld_out,
@@ -712,6 +749,7 @@ void svt_initialise(mc_handle h, const mc_params *prm) {
   h->precision = P.precision;
   h->tau = P.tau > 0 ? P.tau : 5.0 * std::sqrt((double)h->m * (double)h->n);
   // Y currently holds P_Phi(M) only if no rSVD/SVT changed it; start from M.
+  yc_ready(h);
   copy_in(h->stream, h->y.p, h->mval.p, sizeof(float) * h->nnz);
   mirror_values(h->stream, h->nnz, h->perm.as<int>(), h->y.as<float>(), h->yc.as<float>());
   h->normF = std::sqrt(sumsq_values(h, h->mval.as<float>(), h->nnz));
@@ -858,16 +896,17 @@ mc_status svt_step(mc_handle h, mc_iter_info *out) {
   // fused SDDMM + residual + update over Phi, then mirror Y into the CSC copy
   double *sq = reinterpret_cast<double *>(fbuf(h, h->seg_sq, 2 * (size_t)sddmm_partials() + 16));
   int nsq = 0;
+  yc_ready(h);  // the previous copy into CSC order has read Y
   {
     Scope sc(h, MC_T_SDDMM, 20.0 * h->nnz + 4.0 * (double)(h->m + h->n) * ldp, 2.0 * h->nnz * r);
     nsq = sddmm_update(h->stream, h->nnz, h->rix.as<int>(), h->ci.as<int>(), h->mval.as<float>(), h->y.as<float>(),
                        Us, ldp, Vr, ldp, r, (float)P.delta, 1, sq, nullptr);
   }
   h->dsum.reserve(h->alloc, sizeof(double) * 1032);
+  mirror_async(h);  // Y -> CSC order, overlapping what follows
   {
-    Scope sc(h, MC_T_OTHER, 12.0 * h->nnz);
+    Scope sc(h, MC_T_OTHER, 0);
     sum_doubles(h->stream, sq, nsq, h->dsum.as<double>());
-    mirror_values(h->stream, h->nnz, h->perm.as<int>(), h->y.as<float>(), h->yc.as<float>());
   }
   double ssq = 0;
   MC_CUDA(cudaMemcpyAsync(&ssq, h->dsum.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1107,6 +1146,7 @@ mc_status mc_create_coo(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const
 
 void mc_destroy(mc_handle h) {
   if (!h) return;
+  if (h->side) cudaStreamSynchronize(h->side);
   if (h->stream) cudaStreamSynchronize(h->stream);
   Alloc &a = h->alloc;
   for (DBuf *b : {&h->Om_bf, &h->Q_bf, &h->T_bf}) b->release(a);
@@ -1122,13 +1162,25 @@ void mc_destroy(mc_handle h) {
     if (h->stage_ev[q]) cudaEventDestroy(h->stage_ev[q]);
     if (h->h_stage[q]) cudaFreeHost(h->h_stage[q]);
   }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_yc) cudaEventDestroy(h->ev_yc);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+mc_status mc_join(mc_handle h) {
+  if (!h) return MC_EINVAL;
+  return guarded([&]() -> mc_status {
+    yc_ready(h);
+    return MC_OK;
+  });
 }
 
 mc_status mc_set_values(mc_handle h, const float *val) {
   if (!h || (!val && h->nnz > 0)) return MC_EINVAL;
   return guarded([&]() -> mc_status {
+    yc_ready(h);
     copy_in(h->stream, h->y.p, val, sizeof(float) * h->nnz);
     mirror_values(h->stream, h->nnz, h->perm.as<int>(), h->y.as<float>(), h->yc.as<float>());
     sync(h);
@@ -1274,6 +1326,7 @@ mc_status mc_timing_enable(mc_handle h, int on) {
 mc_status mc_timing_read(mc_handle h, mc_timing *out) {
   if (!h || !out) return MC_EINVAL;
   return guarded([&]() -> mc_status {
+    if (h->side) MC_CUDA(cudaStreamSynchronize(h->side));  // events recorded there too
     sync(h);
     h->prof.resolve();
     for (int i = 0; i < MC_T_COUNT; ++i) out[i] = h->prof.acc[i];
