@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 eig_tridiag_small_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d,
                          float *__restrict__ g_e, float *__restrict__ g_beta, float *__restrict__ Hv) {
   __shared__ float S[TS_K * TS_LD];
-  __shared__ float vs[TS_K], ws[TS_K];
+  __shared__ __align__(16) float vs[TS_K];
+  __shared__ __align__(16) float ws[TS_K];
   __shared__ float red[2][2], s_amax[2];
   const int t = threadIdx.x;
   float amax = 0.f;
@@ -134,17 +135,41 @@ eig_tridiag_small_kernel(int K, const float *__restrict__ A, int lda, float *__r
     if (bt == 0.f) continue;  // uniform: every thread has the same sigma
     if (act) vs[t] = vr;
     __syncthreads();
+    // loads in batches of four ahead of their arithmetic: the compiler
+    // cannot tell the row stores below from the vs / ws loads, so a plain
+    // loop pays one shared-memory latency per element
     float p = 0.f;
     if (act) {
-      for (int b = 0; b < n; ++b) p = fmaf(row[b], vs[b], p);
-      p *= bt;
+      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+      int b = 0;
+      for (; b + 4 <= n; b += 4) {
+        const float r0 = row[b], r1 = row[b + 1], r2 = row[b + 2], r3 = row[b + 3];
+        const float4 v4 = *reinterpret_cast<const float4 *>(vs + b);
+        p0 = fmaf(r0, v4.x, p0);
+        p1 = fmaf(r1, v4.y, p1);
+        p2 = fmaf(r2, v4.z, p2);
+        p3 = fmaf(r3, v4.w, p3);
+      }
+      for (; b < n; ++b) p0 = fmaf(row[b], vs[b], p0);
+      p = ((p0 + p1) + (p2 + p3)) * bt;
     }
     const float c = 0.5f * bt * ts_sum(act ? vr * p : 0.f, red, rb);
     const float w = p - c * vr;
     if (act) ws[t] = w;
     __syncthreads();
-    if (act)
-      for (int b = 0; b < n; ++b) row[b] -= vr * ws[b] + w * vs[b];
+    if (act) {
+      int b = 0;
+      for (; b + 4 <= n; b += 4) {
+        const float r0 = row[b], r1 = row[b + 1], r2 = row[b + 2], r3 = row[b + 3];
+        const float4 w4 = *reinterpret_cast<const float4 *>(ws + b);
+        const float4 v4 = *reinterpret_cast<const float4 *>(vs + b);
+        row[b] = r0 - (vr * w4.x + w * v4.x);
+        row[b + 1] = r1 - (vr * w4.y + w * v4.y);
+        row[b + 2] = r2 - (vr * w4.z + w * v4.z);
+        row[b + 3] = r3 - (vr * w4.w + w * v4.w);
+      }
+      for (; b < n; ++b) row[b] -= vr * ws[b] + w * vs[b];
+    }
     __syncthreads();
   }
   if (t == 0) {
