@@ -420,6 +420,62 @@ __global__ void spmm_fixup_kernel(int64_t nsplit, const int *__restrict__ split_
   }
 }
 
+// The same sums with a warp per split row for panels of at most 4 KM4
+// columns: every column group's partials are loaded in one pass over the
+// row's segments (K4 float4 per segment and lane), so the launch has a
+// third (K = 12) as many warps, each with the same few load latencies.  Per
+// column the order is that of spmm_fixup_kernel: the same bits.
+template <int KM4>
+__global__ void spmm_fixup_rows_kernel(int64_t nsplit, const int *__restrict__ split_row,
+                                       const int *__restrict__ split_slot, const float *__restrict__ partial, int K,
+                                       float *__restrict__ out, int ld_out) {
+  const int K4 = K / 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nsplit; i += wstride) {
+    const int s0 = split_slot[i], s1 = split_slot[i + 1];
+    float4 acc[KM4];
+#pragma unroll
+    for (int c = 0; c < KM4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int b = s0 + lane; b < s1; b += 4 * 32) {
+      float4 v[4][KM4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int sg = b + 32 * u;
+#pragma unroll
+        for (int c = 0; c < KM4; ++c)
+          v[u][c] = (sg < s1 && c < K4) ? *reinterpret_cast<const float4 *>(partial + (int64_t)sg * K + 4 * c)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < KM4; ++c) {
+          acc[c].x += v[u][c].x;
+          acc[c].y += v[u][c].y;
+          acc[c].z += v[u][c].z;
+          acc[c].w += v[u][c].w;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < KM4; ++c) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, off);
+        acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, off);
+        acc[c].z += __shfl_xor_sync(0xffffffffu, acc[c].z, off);
+        acc[c].w += __shfl_xor_sync(0xffffffffu, acc[c].w, off);
+      }
+    }
+    if (lane == 0) {
+      float4 *dst = reinterpret_cast<float4 *>(out + (int64_t)split_row[i] * ld_out);
+#pragma unroll
+      for (int c = 0; c < KM4; ++c)
+        if (c < K4) dst[c] = acc[c];
+    }
+  }
+}
+
 // ------------------------------------------------------------ elementwise ---
 __global__ void scale_kernel(int64_t nnz, const float *__restrict__ src, float alpha, float *__restrict__ dst) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
@@ -688,6 +744,22 @@ void launch_seg(int u, int64_t blocks, int threads, cudaStream_t st, int64_t nse
 }
 }  // namespace
 
+// Adds the partials of rows longer than one segment (K columns, a multiple of 4).
+static void launch_fixup(cudaStream_t st, const SegPlan &plan, const float *partial, int K, float *out, int ld_out) {
+  const int K4 = K / 4;
+  const int *sr = plan.split_row.as<int>(), *ss = plan.split_slot.as<int>();
+  if (K4 <= 4)
+    spmm_fixup_rows_kernel<4><<<grid_for(plan.nsplit * 32, 256, 1 << 20), 256, 0, st>>>(plan.nsplit, sr, ss, partial,
+                                                                                       K, out, ld_out);
+  else if (K4 <= 8)
+    spmm_fixup_rows_kernel<8><<<grid_for(plan.nsplit * 32, 256, 1 << 20), 256, 0, st>>>(plan.nsplit, sr, ss, partial,
+                                                                                       K, out, ld_out);
+  else
+    spmm_fixup_kernel<<<grid_for(plan.nsplit * K4 * 32, 256), 256, 0, st>>>(plan.nsplit, sr, ss, partial, K, out,
+                                                                           ld_out);
+  MC_CHECK_LAUNCH();
+}
+
 // Lane groups of a product: from the widest chunk the default chunking uses,
 // so that every chunking the tuner tries fits the same groups.
 int spmm_groups(int K, int64_t rows_in) { return lane_groups(std::min(K, default_chunk(rows_in)) / 4); }
@@ -732,9 +804,7 @@ void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val
 #undef MC_SEG_ARGS
     MC_CHECK_LAUNCH();
     if (plan.nsplit > 0) {
-      spmm_fixup_kernel<<<grid_for(plan.nsplit * (kc / 4) * 32, 256), 256, 0, st>>>(
-          plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, kc, out + c0, ld_out);
-      MC_CHECK_LAUNCH();
+      launch_fixup(st, plan, partial, kc, out + c0, ld_out);
     }
   }
 }
@@ -757,9 +827,7 @@ void spmm_bf16(cudaStream_t st, const SegPlan &plan, const int *idx, const float
 #undef MC_BF_ARGS
   MC_CHECK_LAUNCH();
   if (plan.nsplit > 0) {
-    spmm_fixup_kernel<<<grid_for(plan.nsplit * (K / 4) * 32, 256), 256, 0, st>>>(
-        plan.nsplit, plan.split_row.as<int>(), plan.split_slot.as<int>(), partial, K, out, ld_out);
-    MC_CHECK_LAUNCH();
+    launch_fixup(st, plan, partial, K, out, ld_out);
   }
 }
 

@@ -90,7 +90,7 @@ def _rand_csr(m, n, density, rng, heavy_row=None, heavy_col=None):
     return A
 
 
-@pytest.mark.parametrize("K", [1, 3, 4, 8, 60, 64, 100, 128, 240, 300, 1024])
+@pytest.mark.parametrize("K", [1, 3, 4, 8, 12, 20, 32, 60, 64, 100, 128, 240, 300, 1024])
 def test_spmm_both_ways(mc, K):
     rng = np.random.default_rng(K)
     m, n = 700, 900
