@@ -184,3 +184,24 @@ def test_svt_sample_and_values(mc):
         assert np.allclose(got, want, rtol=1e-5, atol=1e-5)
         y = h.get_values()
         assert y.shape == (o.nnz,) and np.all(np.isfinite(y))
+
+
+def test_products_after_step_see_updated_iterate(mc):
+    """After an SVT step the copy of Y into CSC order runs on the handle's
+    second stream; a Y^T X product issued right after must wait for it and
+    agree with the product of the updated values in CSR order."""
+    o = mc_synth.ratings(m=6000, n=2500, N=400000, seed=11)
+    rng = np.random.default_rng(5)
+    with mc.Handle.from_observed(o) as h:
+        prm = mc.params(tau=5 * math.sqrt(o.m * o.n), delta=1.9, eps=1e-4, recycle=1, seed=3)
+        for step in range(3):
+            h.svt_step(prm)
+            Xt = rng.standard_normal((o.m, 12)).astype(np.float32)
+            got = h.spmm(Xt, trans=True)      # reads the CSC copy immediately
+            y = h.get_values().astype(np.float64)
+            A = as_csr64(o.m, o.n, o.row_ptr, o.col, y)
+            want = A.T @ Xt.astype(np.float64)
+            assert np.max(np.abs(got - want)) < 1e-4 * max(1.0, np.abs(want).max()), step
+        h.join()
+        X = rng.standard_normal((o.n, 12)).astype(np.float32)
+        assert np.array_equal(h.spmm(X), h.spmm(X))
