@@ -184,6 +184,139 @@ eig_tridiag_small_kernel(int K, const float *__restrict__ A, int lda, float *__r
   }
 }
 
+// Householder tridiagonalisation for 64 < K <= 256: a thread per row of
+// the trailing matrix, the lower triangle packed in shared memory.  Row a's
+// product with v reads its own contiguous part (columns <= a) and then walks
+// down its column (entries (b, a), b > a: consecutive threads read
+// consecutive words); the rank-2 update runs row-wise over the lower
+// triangle.  Loads go four at a time ahead of their arithmetic.  Outputs as
+// eig_tridiag_kernel.
+constexpr int TM_K = 256, TM_THREADS = 256;
+
+__device__ __forceinline__ float tm_sum(float v, float (*red)[TM_THREADS / 32], int &rb) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[rb][threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int q = 0; q < TM_THREADS / 32; ++q) t += red[rb][q];
+  rb ^= 1;
+  return t;
+}
+
+__global__ void __launch_bounds__(TM_THREADS, 1)
+eig_tridiag_mid_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d,
+                       float *__restrict__ g_e, float *__restrict__ g_beta, float *__restrict__ Hv) {
+  extern __shared__ __align__(16) float P[];  // packed lower triangle, K (K + 1) / 2
+  __shared__ __align__(16) float vs[TM_K];
+  __shared__ __align__(16) float ws[TM_K];
+  __shared__ float red[2][TM_THREADS / 32], s_amax[TM_THREADS / 32];
+  const int t = threadIdx.x;
+  float amax = 0.f;
+  for (int e = t; e < K * K; e += TM_THREADS) {  // coalesced over A, lower triangle kept
+    const int r = e / K, c = e % K;
+    if (c > r) continue;
+    const float x = A[(int64_t)r * lda + c];
+    P[pk(r, c)] = x;
+    amax = fmaxf(amax, fabsf(x));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+  if ((t & 31) == 0) s_amax[t >> 5] = amax;
+  __syncthreads();
+  amax = 0.f;
+#pragma unroll
+  for (int q = 0; q < TM_THREADS / 32; ++q) amax = fmaxf(amax, s_amax[q]);
+  const float sig_floor = fmaxf((FLT_EPSILON * amax) * (FLT_EPSILON * amax), 1e-37f);
+  int rb = 0;
+  for (int i = 0; i + 2 < K; ++i) {
+    const int n = K - 1 - i;
+    const bool act = t < n;
+    const int ga = i + 1 + t;  // this thread's row
+    const float x = act ? P[pk(ga, i)] : 0.f;
+    const float sigma = tm_sum(act && t >= 1 ? x * x : 0.f, red, rb);
+    const float x0 = P[pk(i + 1, i)];
+    float bt = 0.f, alpha = x0, v0 = 0.f;
+    if (sigma > sig_floor) {
+      const float mu = sqrtf(x0 * x0 + sigma);
+      alpha = x0 <= 0.f ? mu : -mu;
+      v0 = x0 - alpha;
+      bt = 2.0f / (v0 * v0 + sigma);
+    }
+    const float vr = t == 0 ? v0 : x;
+    if (t == 0) {
+      g_d[i] = P[pk(i, i)];
+      g_e[i] = alpha;
+      g_beta[i] = bt;
+    }
+    if (act) Hv[(int64_t)i * K + t] = vr;
+    if (bt == 0.f) continue;  // uniform
+    if (act) vs[t] = vr;
+    __syncthreads();
+    float p = 0.f;
+    float *row = P + pk(ga, i + 1);  // row ga, columns i + 1 .. ga
+    if (act) {
+      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+      int b = 0;
+      for (; b + 4 <= t + 1; b += 4) {
+        const float r0 = row[b], r1 = row[b + 1], r2 = row[b + 2], r3 = row[b + 3];
+        const float4 v4 = *reinterpret_cast<const float4 *>(vs + b);
+        p0 = fmaf(r0, v4.x, p0);
+        p1 = fmaf(r1, v4.y, p1);
+        p2 = fmaf(r2, v4.z, p2);
+        p3 = fmaf(r3, v4.w, p3);
+      }
+      for (; b <= t; ++b) p0 = fmaf(row[b], vs[b], p0);
+      // column part: entries (i + 1 + b, ga) for b > t
+      int idx = pk(i + 1 + b, ga);
+      for (; b + 4 <= n; b += 4) {
+        const int gb = i + 1 + b;
+        const int i1 = idx + gb + 1, i2 = i1 + gb + 2, i3 = i2 + gb + 3;
+        const float r0 = P[idx], r1 = P[i1], r2 = P[i2], r3 = P[i3];
+        p0 = fmaf(r0, vs[b], p0);
+        p1 = fmaf(r1, vs[b + 1], p1);
+        p2 = fmaf(r2, vs[b + 2], p2);
+        p3 = fmaf(r3, vs[b + 3], p3);
+        idx = i3 + gb + 4;
+      }
+      for (; b < n; ++b) {
+        p0 = fmaf(P[idx], vs[b], p0);
+        idx += i + 2 + b;
+      }
+      p = ((p0 + p1) + (p2 + p3)) * bt;
+    }
+    const float c = 0.5f * bt * tm_sum(act ? vr * p : 0.f, red, rb);
+    const float w = p - c * vr;
+    if (act) ws[t] = w;
+    __syncthreads();
+    if (act) {
+      int b = 0;
+      for (; b + 4 <= t + 1; b += 4) {
+        const float r0 = row[b], r1 = row[b + 1], r2 = row[b + 2], r3 = row[b + 3];
+        const float4 w4 = *reinterpret_cast<const float4 *>(ws + b);
+        const float4 v4 = *reinterpret_cast<const float4 *>(vs + b);
+        row[b] = r0 - (vr * w4.x + w * v4.x);
+        row[b + 1] = r1 - (vr * w4.y + w * v4.y);
+        row[b + 2] = r2 - (vr * w4.z + w * v4.z);
+        row[b + 3] = r3 - (vr * w4.w + w * v4.w);
+      }
+      for (; b <= t; ++b) row[b] -= vr * ws[b] + w * vs[b];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (K >= 2) {
+      g_d[K - 2] = P[pk(K - 2, K - 2)];
+      g_e[K - 2] = P[pk(K - 1, K - 2)];
+      g_beta[K - 2] = 0.f;
+    }
+    g_d[K - 1] = P[pk(K - 1, K - 1)];
+    g_e[K - 1] = 0.f;
+    g_beta[K - 1] = 0.f;
+  }
+}
+
 template <int PPR, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
 eig_tridiag_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d, float *__restrict__ g_e,
@@ -1106,6 +1239,12 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   } else if (K <= TS_K) {
     eig_tridiag_small_kernel<<<1, TS_THREADS, 0, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                        gw + pl.g_hv);
+  } else if (K <= TM_K) {
+    const size_t smem = sizeof(float) * ((size_t)K * (K + 1) / 2);
+    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float) * (TM_K * (TM_K + 1) / 2))));
+    eig_tridiag_mid_kernel<<<1, TM_THREADS, smem, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                        gw + pl.g_hv);
   } else if (tc.ppr == 2) {
     MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
     eig_tridiag_kernel<2, 256><<<1, 256, pl.tri_smem, st>>>(MC_TRI_ARGS);
