@@ -145,6 +145,7 @@ struct mc_handle_s {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_yc = nullptr;
   bool yc_pending = false;
+  bool single_stream = false;  // the copy stays on the main stream
   Alloc alloc;
   // CSR (rix: row of every entry)
   DBuf rp, ci, mval, y, rix;
@@ -185,6 +186,13 @@ struct mc_handle_s {
   double last_err = 0;
   Prof prof;
 };
+
+
+namespace mc {
+void handle_single_stream(mc_handle h) {
+  if (h) h->single_stream = true;
+}
+}  // namespace mc
 
 namespace {
 
@@ -280,6 +288,11 @@ void yc_ready(mc_handle h) {
 // already on the main stream.
 void mirror_async(mc_handle h) {
   yc_ready(h);
+  if (h->single_stream) {
+    Scope sc(h, MC_T_OTHER, 12.0 * h->nnz);
+    mirror_values(h->stream, h->nnz, h->perm.as<int>(), h->y.as<float>(), h->yc.as<float>());
+    return;
+  }
   if (!h->side) {
     MC_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     MC_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));

@@ -30,6 +30,11 @@ struct Err {
 // Every kernel launch of the library goes through MC_CHECK_LAUNCH, which also
 // counts it (mc_launch_count).
 void count_launch();
+// Keeps the copy of Y into CSC order on the handle's own stream (no second
+// stream): the serving form runs many handles at once, and twice as many
+// streams as hardware work queues would put unrelated jobs' work behind a
+// second stream's event wait.
+void handle_single_stream(mc_handle h);
 #define MC_CHECK_LAUNCH()          \
   do {                             \
     MC_CUDA(cudaGetLastError());   \

@@ -127,6 +127,7 @@ void run_job(mc_server_s *S, Job *J) {
     J->error = mc_last_error();
     return;
   }
+  mc::handle_single_stream(h);  // many jobs share the GPU's work queues
   mc_iter_info info{};
   mc_status last = MC_OK;
   int it = 0;
