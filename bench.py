@@ -308,7 +308,17 @@ def run_ours(args, rank, world, local):
                 "traffic_source": ("ncu DRAM bytes of the SpMM on a 1.6e7-pair case, scaled to this launch by "
                                    "algorithmic bytes" if tr else None),
                 "algorithmic_bytes_per_launch": sp_bytes / max(sp_launch, 1),
+                "lts_pct_of_peak": tr.get("l2_throughput_pct_of_peak") if tr else None,
+                "l1_pct_of_peak": tr.get("l1_throughput_pct_of_peak") if tr else None,
                 "share_of_step": round(sp_ms / t_ms, 3) if t_ms > 0 else None}
+    # the fused update's fraction of HBM, from the per-class pass
+    sd = tm_all["sddmm"]
+    if sd["ms"] > 0 and sd["launches"] > 0:
+        sd_gbs = (sd["bytes"] / 1e9) / (sd["ms"] / 1e3)
+        roofline["sddmm"] = {"achieved": round(sd_gbs, 1), "unit": "GB/s", "frac": round(sd_gbs / peak, 4),
+                             "bytes_per_launch": round(sd["bytes"] / sd["launches"]),
+                             "bytes_model": "20 per observed entry (column, row, M, Y read and write) + the "
+                                            "factor panels; per-class pass after the timed steps"}
     # ---- mixed-precision form: same workload, bf16 Krylov panels ---------------
     hm = mc.Handle(o.m, o.n, o.row_ptr, o.col, o.val, stream=stream)
     prm_m = svt_params(mc, o)
