@@ -1144,10 +1144,9 @@ struct TriCfg {
   int ppr, threads;
 };
 TriCfg tri_cfg(int K) {
-  // rows of the trailing matrix are at most K - 1 long: PPR x 32 >= K - 1
-  // (a smaller PPR unrolls fewer predicated-off columns per row)
-  if (K - 1 <= 64) return {2, 256};
-  if (K <= SMALL_K) return {4, 256};
+  // the warp-per-row kernel serves K > 256 when the cooperative one cannot be
+  // launched (K <= 256 has the row-per-thread kernels); rows of the trailing
+  // matrix are at most K - 1 long: PPR x 32 >= K - 1
   if (K - 1 <= 256) return {8, 1024};
   if (K - 1 <= 512) return {16, 1024};
   return {32, 512};
@@ -1245,12 +1244,6 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
                                  (int)(sizeof(float) * (TM_K * (TM_K + 1) / 2))));
     eig_tridiag_mid_kernel<<<1, TM_THREADS, smem, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                         gw + pl.g_hv);
-  } else if (tc.ppr == 2) {
-    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
-    eig_tridiag_kernel<2, 256><<<1, 256, pl.tri_smem, st>>>(MC_TRI_ARGS);
-  } else if (tc.ppr == 4) {
-    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
-    eig_tridiag_kernel<4, 256><<<1, 256, pl.tri_smem, st>>>(MC_TRI_ARGS);
   } else if (tc.ppr == 8) {
     MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
     eig_tridiag_kernel<8, 1024><<<1, 1024, pl.tri_smem, st>>>(MC_TRI_ARGS);

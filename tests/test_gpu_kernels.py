@@ -36,7 +36,8 @@ def _spd(K, spectrum, rng):
 
 
 @pytest.mark.parametrize("K,kw,kind", [(1, 1, "rand"), (2, 2, "rand"), (8, 5, "rand"), (60, 50, "decay"),
-                                        (64, 64, "cluster"), (240, 50, "rating"), (252, 60, "zeros"),
+                                        (64, 64, "cluster"), (65, 20, "decay"), (100, 30, "cluster"),
+                                        (129, 3, "rating"), (240, 50, "rating"), (252, 60, "zeros"),
                                         (300, 80, "decay"), (400, 100, "decay"), (1024, 40, "decay")])
 def test_eig_topk(mc, K, kw, kind):
     rng = np.random.default_rng(K * 7 + kw)
