@@ -319,8 +319,10 @@ mc_status mc_eig_sym(int K, int kw, const float *A, float *lam, float *W);
  * block at a time; the span is that of Theorem 2): out (R x K) = an
  * orthonormal basis of (I - Qp Qp^T) X.  X is projected against the cols
  * earlier orthonormal columns Qp twice (block classical Gram-Schmidt with
- * reorthogonalisation), then passed through three CholeskyQR steps (the
- * first with a shift of 1e-6 trace/K, then two plain ones).  A column whose
+ * reorthogonalisation), then passed through CholeskyQR steps (the first
+ * with a shift of 1e-6 trace/K, then plain ones: two, or one when the block
+ * is already orthonormal to within 1e-2 after the first, for blocks of at
+ * most 32 columns that take the one-launch kernel).  A column whose
  * squared norm after the projection is at most 1e-10 of its squared norm
  * before (a dependent direction), or whose Cholesky pivot falls to the
  * float32 noise floor, is returned as a zero column.  These are the kernels

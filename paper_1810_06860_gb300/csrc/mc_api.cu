@@ -537,8 +537,8 @@ void draw_omega(mc_handle h, int kb, int kbp, uint64_t seed, uint64_t call_id, c
 // products (Omega, A^T Q_{i-1} and Q_{i-1}) are read as bf16; sums stay
 // float32 and the basis is orthonormalised in float32.
 // The whole block step (norms, two projections against the first cols
-// columns of Qp, CholeskyQR x3) as one cooperative launch for narrow blocks;
-// false when it does not apply (the caller runs the separate kernels).
+// columns of Qp, the CholeskyQR passes) as one cooperative launch for narrow
+// blocks; false when it does not apply (the caller runs the separate kernels).
 // MC_ORTH_FUSED=0 turns it off.
 bool orth_block_fused(mc_handle h, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
                       int ldo) {
@@ -554,7 +554,9 @@ bool orth_block_fused(mc_handle h, int64_t R, int K, float *X, int ldx, const fl
 
 // Steps 3-7 of Alg. 5 for one block: out = an orthonormal basis of
 // (I - Qp Qp^T) X (X clobbered), one cooperative launch for narrow blocks,
-// else norms, two projections and three CholeskyQR passes as separate kernels.
+// else norms, two projections and three CholeskyQR passes as separate kernels
+// (the one-launch form skips the third pass when the second leaves the block
+// orthonormal to within 1e-2).
 void orth_step(mc_handle h, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
                int ldo) {
   if (orth_block_fused(h, R, K, X, ldx, Qp, ldq, cols, out, ldo)) return;

@@ -185,11 +185,14 @@ void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *
 // X 16-byte aligned.  partial: gram_tc_scratch_floats(R, K) floats.  err
 // (device int, may be NULL) receives a nonzero code if a bounded wait expired.
 // One cooperative launch for a narrow Krylov block (K <= 32): column norms
-// (use_ref), two projections against Qp (R x cols), three CholeskyQR passes
-// (first shifted by shift_rel * trace / K and with the dependence test
-// G_jj <= ref_tol * norm_j^2), result into out.  Returns false (nothing
-// launched) when the rows do not fit the CTAs' shared memory or the device
-// has no cooperative launch; the caller then takes the separate kernels.
+// (use_ref), two projections against Qp (R x cols), CholeskyQR passes (the
+// first shifted by shift_rel * trace / K and with the dependence test
+// G_jj <= ref_tol * norm_j^2; the third skipped when the second pass's Gram
+// is within 1e-2 of I), result into out.  Qp's rows are staged in shared
+// memory when they fit, else read from global memory.  Returns false
+// (nothing launched) when the block's rows do not fit the CTAs' shared
+// memory, rows are not 16-byte aligned, or the device has no cooperative
+// launch; the caller then takes the separate kernels.
 size_t orth_narrow_scratch_floats(int64_t R, int K, int cols);
 bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const float *Qp, int ldq, int cols, float *out,
                  int ldo, bool use_ref, float shift_rel, float ref_tol, float *scratch);
