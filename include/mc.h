@@ -304,7 +304,7 @@ int64_t mc_server_admit_order(mc_server s, uint64_t *ids, int64_t cap);
 mc_status mc_omega(int64_t n, int k, uint64_t seed, uint64_t call_id, int col0, float *out,
                    uint32_t *words);
 
-/* Sparse products with the current Y (L108-113 style products of Alg. 5):
+/* Sparse products with the current Y (the A X and A^T X products of Alg. 5):
  * trans = 0: out (m x k) = Y X with X n x k;  trans = 1: out (n x k) = Y^T X
  * with X m x k.  Row-major, host or device. */
 mc_status mc_spmm(mc_handle h, int trans, int k, const float *X, float *out);
