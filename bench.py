@@ -12,6 +12,9 @@ is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The timed steps run with CUDA events around the sparse products only (the
+roofline's kernel); the per-class breakdown (``timing_ms``) comes from as
+many further steps, since events around every launch would slow the step.
 Prints one JSON line (rank 0).  ``--impl reference`` times the float64 CPU
 oracle (the only other implementation of this method here) on the same
 workload on the host cores.
