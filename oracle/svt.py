@@ -68,6 +68,22 @@ def spectral_norm(A: sp.csr_matrix, seed: int = 0, rtol: float = 1e-10, max_iter
     return math.sqrt(lam)
 
 
+def adapt_p(p: int, streak: int, err: float, prev_err: float, p_min: int = 3, p_max: int = 20):
+    """The power-parameter rule stated after Alg. 6 (Sec. IV.C): p grows by one
+    when the relative error of step 16 increases, and falls by one after the
+    error has decreased ten times in a row.  Readings: both comparisons are
+    strict, an unchanged error ends the streak, every change of p restarts it,
+    and p stays within [p_min, p_max].  Returns the new (p, streak)."""
+    if err > prev_err:
+        return min(p + 1, p_max), 0
+    if err < prev_err:
+        streak += 1
+        if streak == 10:
+            return max(p - 1, p_min), 0
+        return p, streak
+    return p, 0
+
+
 def sample_lowrank(rows: np.ndarray, cols: np.ndarray, Us: np.ndarray, V: np.ndarray,
                    chunk: int = 1 << 20) -> np.ndarray:
     """Entries (Us V^T)_{ij} at the listed positions (the X^i of Alg. 6 step 15
@@ -90,8 +106,11 @@ class SvtResult:
 
 
 def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, p0=3, p_min=3,
-             p_max=20, i_max=1000, i_reuse=50, q_reuse=10, recycle=1, seed=0, callback=None) -> SvtResult:
-    """Alg. 6.  ``recycle``: 0 none, 1 reuse Q, 2 reuse U, 3 warm-started Omega."""
+             p_max=20, i_max=1000, i_reuse=50, q_reuse=10, recycle=1, seed=0, callback=None,
+             on_factors=None) -> SvtResult:
+    """Alg. 6.  ``recycle``: 0 none, 1 reuse Q, 2 reuse U, 3 warm-started Omega.
+    ``callback(rec)`` receives each iteration's record; ``on_factors(rec, Us,
+    V)`` also the factors of X^i (for metrics that need the estimate)."""
     A = as_csr64(m, n, row_ptr, col, val)
     M = A.data.copy()
     rows = np.repeat(np.arange(m), np.diff(np.asarray(row_ptr)))
@@ -148,9 +167,10 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
                 recycled = True
                 used_recycle = True
             nsvd += 1
-            margin = min(margin, float(np.min(np.abs(S - tau))) / tau)
+            if S.size:
+                margin = min(margin, float(np.min(np.abs(S - tau))) / tau)
             k += l
-            if S[-1] <= tau:
+            if S.size == 0 or S[-1] <= tau:
                 break
             if kk >= min(m, n) - s:  # cannot grow further
                 break
@@ -164,23 +184,16 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
         x = sample_lowrank(rows, cols, Us, Vr)
         err = float(np.linalg.norm(x - M)) / normF
         rec = dict(i=it, k=int(kk), r=r, p=int(p), err=err, nsvd=nsvd, recycled=used_recycle,
-                   sigma_last=float(S[-1]), sigma_max=float(S[0]), c=c, norm2=norm2, tau_margin=margin)
+                   sigma_last=float(S[-1]) if S.size else 0.0, sigma_max=float(S[0]) if S.size else 0.0, c=c, norm2=norm2, tau_margin=margin)
         history.append(rec)
         if callback is not None:
             callback(rec)
+        if on_factors is not None:
+            on_factors(rec, Us, Vr)
         if err < eps:
             return SvtResult(Us, Vr, sig, it, err, True, history)
         Y.data = Y.data + delta * (M - x)
-        if err > prev_err:
-            p = min(p + 1, p_max)
-            streak = 0
-        elif err < prev_err:
-            streak += 1
-            if streak == 10:
-                p = max(p - 1, p_min)
-                streak = 0
-        else:
-            streak = 0
+        p, streak = adapt_p(p, streak, err, prev_err, p_min, p_max)
         prev_err = err
     return SvtResult(Us, Vr, sig, it, err, False, history)
 

@@ -86,11 +86,17 @@ def c1():
     return mc_synth.lowrank_uniform(500, 500, 10, frac=0.2, seed=0)
 
 
-def test_alg6_matches_alg2_on_config1(c1):
+@pytest.fixture(scope="module")
+def c1_exact(c1):
+    """Alg. 2 with an exact SVD on config 1 (the reference for the Alg. 6 pins)."""
+    return svt.svt_exact(c1.m, c1.n, c1.row_ptr, c1.col, c1.val, tau=2500.0, delta=6.0, eps=1e-4, seed=0)
+
+
+def test_alg6_matches_alg2_on_config1(c1, c1_exact):
     """Sec. IV.C / V.B: fast SVT behaves as SVT with an exact truncated SVD --
     same iteration count and error, and exact recovery of the rank-10 M."""
     kw = dict(tau=2500.0, delta=6.0, eps=1e-4, seed=0)
-    ex = svt.svt_exact(c1.m, c1.n, c1.row_ptr, c1.col, c1.val, **kw)
+    ex = c1_exact
     fa = svt.svt_fast(c1.m, c1.n, c1.row_ptr, c1.col, c1.val, recycle=3, **kw)
     assert ex.converged and fa.converged
     assert abs(ex.iters - fa.iters) <= 2
@@ -126,3 +132,81 @@ def test_metrics():
     assert abs(metrics.max_principal_angle(A, B) - th) < 1e-12
     assert metrics.sigma_rel_err(np.array([1.0, 2.2]), np.array([1.0, 2.0])) == pytest.approx(0.1)
     assert metrics.completion_error(np.array([0.0, 0.0]), np.array([3.0, 4.0])) == 1.0
+
+
+@pytest.fixture(scope="module")
+def c1_recycle_q(c1):
+    return svt.svt_fast(c1.m, c1.n, c1.row_ptr, c1.col, c1.val, tau=2500.0, delta=6.0, eps=1e-4, seed=0,
+                        recycle=1, i_reuse=5, q_reuse=2)
+
+
+def test_recycle_q_matches_alg2_on_config1(c1, c1_exact, c1_recycle_q):
+    """Sec. IV.B strategy 1 (restart Alg. 5 at step 8 with the stored Q) inside
+    Alg. 6: with recycling from iteration 5, two recycled calls per fresh
+    basis, the iteration count, the recovered matrix and its rank are those of
+    Alg. 2 with an exact SVD (the claim of Sec. IV.C and Sec. V that recycling
+    does not change the result)."""
+    fa = c1_recycle_q
+    ex = c1_exact
+    assert ex.converged and fa.converged
+    assert abs(fa.iters - ex.iters) <= 2
+    h = fa.history
+    assert not any(x["recycled"] for x in h[:4])
+    rec = [x["recycled"] for x in h[4:]]
+    assert sum(rec) >= len(rec) // 2  # two recycled calls per fresh basis
+    # after each fresh basis, at most q_reuse recycled iterations in a row
+    run = best = 0
+    for x in rec:
+        run = run + 1 if x else 0
+        best = max(best, run)
+    assert best <= 2
+    X = fa.Us @ fa.V.T
+    assert np.linalg.norm(X - c1.dense) / np.linalg.norm(c1.dense) < 1e-3
+    assert fa.V.shape[1] == ex.V.shape[1] == 10
+    Xe = ex.Us @ ex.V.T
+    assert np.linalg.norm(X - Xe) / np.linalg.norm(Xe) < 1e-3
+
+
+def test_p_rule_on_error_sequence():
+    """The p rule after Alg. 6 (Sec. IV.C) on a hand-written error sequence:
+    +1 on every increase, -1 after ten strict decreases in a row, the streak
+    broken by an increase or an unchanged error, p kept in [p_min, p_max]."""
+    def run(errs, p=5, p_min=3, p_max=7):
+        streak, prev, ps = 0, math.inf, []
+        for e in errs:
+            p, streak = svt.adapt_p(p, streak, e, prev, p_min, p_max)
+            prev = e
+            ps.append(p)
+        return ps
+
+    dec = [1.0 - 0.01 * j for j in range(31)]  # 31 strict decreases after the first (inf -> 1.0 counts too)
+    ps = run(dec)
+    # decreases number 10, 20 and 30 (counting the first from inf) lower p by one each, down to p_min = 3
+    assert ps[8] == 5 and ps[9] == 4 and ps[18] == 4 and ps[19] == 3 and ps[29] == 3 and ps[30] == 3
+    # an increase raises p and restarts the streak
+    ps = run([1.0, 0.9, 0.95] + [0.9 - 0.01 * j for j in range(10)])
+    assert ps[:3] == [5, 5, 6] and ps[11] == 6 and ps[12] == 5
+    # an unchanged error ends the streak without changing p
+    head = [1.0] + [0.9 - 0.01 * j for j in range(8)]  # nine strict decreases (from inf)
+    ps = run(head + [head[-1]] + [0.8 - 0.01 * j for j in range(9)])
+    assert ps == [5] * 19
+    ps = run(head + [head[-1]] + [0.8 - 0.01 * j for j in range(10)])
+    assert ps[-1] == 4 and ps[:-1] == [5] * 19
+    # increases saturate at p_max
+    assert run([1.0, 2.0, 3.0, 4.0, 5.0, 6.0])[-1] == 7
+
+
+def test_svt_fast_follows_p_rule(c1_recycle_q):
+    """The p recorded per iteration of Alg. 6 replays the rule from the
+    recorded errors, and the trajectory exercises both branches."""
+    h = c1_recycle_q.history
+    p, streak, prev = h[0]["p"], 0, math.inf
+    ups = downs = 0
+    for a, b in zip(h[:-1], h[1:]):
+        assert a["p"] == p
+        p2, streak = svt.adapt_p(p, streak, a["err"], prev, 3, 20)
+        ups += p2 > p
+        downs += p2 < p
+        p, prev = p2, a["err"]
+        assert b["p"] == p
+    assert ups >= 1 and downs >= 1
