@@ -1348,6 +1348,9 @@ extern "C" mc_status mc_gram_noalloc(int64_t R, int K, const float *X, int ld, f
     MC_REQUIRE(X != nullptr && G != nullptr, "mc_gram_noalloc: null X or G");
     MC_REQUIRE(ld >= K && ld % 4 == 0, "mc_gram_noalloc: ld must be >= K and a multiple of 4");
     MC_REQUIRE(ldg >= K, "mc_gram_noalloc: ldg must be >= K");
+    // the kernel reads rows of X as float4: the base must be 16-byte aligned
+    MC_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15u) == 0, "mc_gram_noalloc: X must be 16-byte aligned");
+    MC_REQUIRE(is_device_ptr(X) && is_device_ptr(G), "mc_gram_noalloc: X and G must be device pointers");
     const int Kp = static_cast<int>(round_up(K, TN_T));
     const size_t tile_floats = (size_t)Kp * Kp;
     if (tile_floats > kNoAllocScratchFloats)
@@ -1374,5 +1377,11 @@ extern "C" mc_status mc_gram_noalloc(int64_t R, int K, const float *X, int ld, f
   } catch (const Err &e) {
     set_error(e.msg);
     return e.st;
+  } catch (const std::bad_alloc &) {
+    set_error("mc_gram_noalloc: host allocation failed");
+    return MC_ENOMEM;
+  } catch (const std::exception &e) {
+    set_error(std::string("mc_gram_noalloc: ") + e.what());
+    return MC_EINTERNAL;
   }
 }

@@ -606,6 +606,7 @@ void coo_to_csr(cudaStream_t st, Alloc &a, int64_t m, int64_t n, int64_t nnz, co
   }
   const int64_t ntile = (nnz + RS_TILE - 1) / RS_TILE;
   DBuf k0, k1, v0, v1, hist, offs, cnt, rp32;
+  BufGuard guard(a, {&k0, &k1, &v0, &v1, &hist, &offs, &cnt, &rp32});
   k0.reserve(a, sizeof(unsigned long long) * nnz);
   k1.reserve(a, sizeof(unsigned long long) * nnz);
   v0.reserve(a, sizeof(int) * nnz);

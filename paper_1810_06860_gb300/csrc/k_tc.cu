@@ -173,8 +173,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
     const int y = static_cast<int>(r0 + (int64_t)s * TC_KT);
     for (int j = 0; j < nbox; ++j) tma_load_2d(raw[b] + j * TC_BOX_BYTES, &xmap, 32 * j, y, &full_bar[b]);
   };
+  // tid 0 issues every load and every MMA: it alone tracks how far both got,
+  // for a clean exit after an expired wait
+  int issued = 0, committed = -1;
   if (tid == 0)
-    for (int s = 0; s < S && s < 2; ++s) issue_loads(s, s);
+    for (; issued < S && issued < 2; ++issued) issue_loads(issued, issued);
 
   const uint32_t id0 = idesc_tf32(128, N0);
   const uint32_t id1 = idesc_tf32(128, 128);
@@ -231,24 +234,25 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
         }
       }
       mma_commit(&mma_bar[b]);
-      if (s + 2 < S) issue_loads(s + 2, b);
+      committed = s;
+      if (s + 2 < S) {
+        issue_loads(s + 2, b);
+        issued = s + 3;
+      }
     }
   }
   __syncthreads();
-  // wait for the last MMAs, then read the accumulators
-  bool have = S > 0 && !s_fail;
-  if (S > 0) {
-    const int sl = S - 1;
-    if (!mbar_wait(&mma_bar[sl & 1], (sl >> 1) & 1)) {
-      atomicOr(&s_fail, 2);
-      have = false;
-    }
-  }
-  // drain loads still in flight after an early exit
-  if (s_fail && tid == 0) {
-    for (int b = 0; b < 2; ++b) mbar_wait(&full_bar[b], 0), mbar_wait(&full_bar[b], 1);
+  if (tid == 0) {
+    // The last commit covers every MMA issued before it: wait for it.  Then
+    // wait for the loads of stages that no MMA consumed (only after an early
+    // exit): on each barrier the phase waited for is the latest one armed, so
+    // a completed phase returns at once.  All waits are bounded.
+    if (committed >= 0 && !mbar_wait(&mma_bar[committed & 1], (committed >> 1) & 1)) atomicOr(&s_fail, 2);
+    for (int t = committed + 1; t < issued; ++t) mbar_wait(&full_bar[t & 1], (t >> 1) & 1);
   }
   __syncthreads();
+  // read the accumulators only after a complete run
+  const bool have = S > 0 && !s_fail;
   tc_fence_after();
   float *out = partial + (size_t)blockIdx.x * Kp * Kp;
   const int row = 32 * wid + lane;  // accumulator lane = row within the tile
@@ -258,13 +262,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
     const int gcol0 = tile * 128;
     const uint32_t tcol = tile == 0 ? 0u : static_cast<uint32_t>(N0);
     for (int c = 0; c < ncols; c += 16) {
-      float v[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(32 * wid) << 16) + tcol + c, v);
+      float v[16] = {};
+      // have is the same in every thread: the warp-wide load is skipped as a whole
+      if (have) tmem_ld16(tmem + (static_cast<uint32_t>(32 * wid) << 16) + tcol + c, v);
       if (grow < Kp) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int gc = gcol0 + c + i;
-          if (gc < Kp) out[(size_t)grow * Kp + gc] = have ? v[i] : 0.f;
+          if (gc < Kp) out[(size_t)grow * Kp + gc] = v[i];
         }
       }
     }

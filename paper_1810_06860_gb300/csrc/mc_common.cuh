@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -63,6 +64,19 @@ struct DBuf {
   T *as() const { return static_cast<T *>(p); }
   void reserve(Alloc &a, size_t bytes);   // contents not preserved
   void release(Alloc &a);
+};
+
+// Releases the listed buffers when it leaves scope, so a temporary buffer is
+// returned to the allocator also when a later step throws.
+struct BufGuard {
+  Alloc &a;
+  std::vector<DBuf *> bufs;
+  BufGuard(Alloc &a_, std::initializer_list<DBuf *> b) : a(a_), bufs(b) {}
+  BufGuard(const BufGuard &) = delete;
+  BufGuard &operator=(const BufGuard &) = delete;
+  ~BufGuard() {
+    for (DBuf *b : bufs) b->release(a);
+  }
 };
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
