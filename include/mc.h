@@ -145,6 +145,14 @@ mc_status mc_set_precision(mc_handle h, int precision);
 mc_status mc_rsvd_pi(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U,
                      float *S, float *V, int *k_out);
 
+/* mc_rsvd_basic: as mc_rsvd_bki but by the basic randomized SVD with power
+ * iteration (Alg. 1, Sec. II.B): Q = orth(Y Omega), then p times
+ * G = orth(Y^T Q), Q = orth(Y G) -- an orthonormalisation after every
+ * product -- then B^T = Y^T Q and the SVD of B (computed by eigSVD, which
+ * Lemma 1 shows equal to svd()).  The cost reference of Table I. */
+mc_status mc_rsvd_basic(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U,
+                        float *S, float *V, int *k_out);
+
 /* mc_svt_step: one outer iteration of Alg. 6 (steps 3-17).  The first call on
  * a handle (or the first after mc_svt_reset) also performs step 1: estimates
  * ||P_Phi(M)||_2, sets c and Y^0 = c delta P_Phi(M).  params is read at that
@@ -348,8 +356,9 @@ mc_status mc_gram(int64_t R, int K, const float *X, float *G);
 mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G);
 
 /* mc_gram_noalloc: G = X^T X (K x K, leading dimension ldg) of a tall device
- * matrix X (R rows, K columns, leading dimension ld, ld a multiple of 4), like
- * mc_gram but without allocating any device memory.  The paper has no
+ * matrix X (R rows, K columns, leading dimension ld, ld a multiple of 4, base
+ * address 16-byte aligned), like mc_gram but without allocating any device
+ * memory.  Columns K..ld-1 of X are never combined into G.  The paper has no
  * counterpart; it exists for callers that cannot allocate while they call:
  * code between cudaStreamBeginCapture and cudaStreamEndCapture, host
  * callbacks and allocator hooks, and hosts whose device memory is entirely
@@ -362,7 +371,11 @@ mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G);
  *     with MC_EINVAL (the array must hold one 1024 x 1024 partial tile).
  *   - The first call on a device looks up that array's device address with
  *     cudaGetSymbolAddress (with the device current) and caches it; make that
- *     first call before any stream capture.
+ *     first call before any stream capture.  The cached address belongs to
+ *     the device's primary context: after cudaDeviceReset the library must
+ *     not be called again in that process.
+ *   - MC_EINVAL (nothing enqueued) for R or K < 1, null, host or unaligned
+ *     pointers, ld < K or not a multiple of 4, ldg < K, K > 1024.
  *   - All calls share the array and each overwrites it: calls that can
  *     overlap on the GPU (different streams, no ordering between them) race
  *     and give wrong results.  Order them on one stream or with events. */

@@ -181,7 +181,9 @@ class Handle:
         pv, _ = _ptr(V, np.float32)
         _check(fn(self._h, k, s, p, seed, call_id, pu, ps, pv, C.byref(ko)), fn.__name__)
         kk = ko.value
-        return U[:, :kk], S[:kk], V[:, :kk]
+        # the library writes m x k_out and n x k_out densely at the buffers' start
+        return (U.reshape(-1)[:self.m * kk].reshape(self.m, kk), S[:kk],
+                V.reshape(-1)[:self.n * kk].reshape(self.n, kk))
 
     def rsvd_bki(self, k: int, s: int = 10, p: int = 3, seed: int = 0, call_id: int = 0, device: bool = False):
         """Alg. 5: rank-k SVD (U, S descending, V) of the current iterate."""
@@ -192,6 +194,10 @@ class Handle:
         return self._rsvd(self._lib.mc_rsvd_pi, k, s, p, seed, call_id, device)
 
     # ---- SVT ---------------------------------------------------------------
+    def rsvd_basic(self, k: int, s: int = 10, p: int = 3, seed: int = 0, call_id: int = 0, device: bool = False):
+        """Basic rSVD with power iteration (Alg. 1): (U, S, V)."""
+        return self._rsvd(self._lib.mc_rsvd_basic, k, s, p, seed, call_id, device)
+
     def svt_step(self, prm: McParams | None = None) -> dict:
         info = McIterInfo()
         _check(self._lib.mc_svt_step(self._h, C.byref(prm) if prm is not None else None, C.byref(info)),
@@ -221,6 +227,18 @@ class Handle:
         rr = C.c_int(0)
         _check(self._lib.mc_svt_factors(self._h, r, pu, pv, ps, C.byref(rr)), "mc_svt_factors")
         return Us, V, sg
+
+    def factors_into(self, Us, V, sigma) -> int:
+        """Copy the factors of the current estimate into caller buffers of
+        capacity max_r = Us.shape[1] columns (Us: m x r, V: n x r and sigma: r
+        written densely at the start of each buffer); returns r."""
+        cap = int(Us.shape[1])
+        pu, _ = _ptr(Us, np.float32)
+        pv, _ = _ptr(V, np.float32)
+        ps, _ = _ptr(sigma, np.float32)
+        r = C.c_int(0)
+        _check(self._lib.mc_svt_factors(self._h, cap, pu, pv, ps, C.byref(r)), "mc_svt_factors")
+        return r.value
 
     def sample(self, rows, cols, device: bool = False):
         rows = rows if _is_torch(rows) else np.ascontiguousarray(rows, np.int64)

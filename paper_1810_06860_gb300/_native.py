@@ -69,6 +69,7 @@ _SIGS = {
     "mc_get_values": (C.c_int, [_P, _P]),
     "mc_rsvd_bki": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, _P, _P, _P, C.POINTER(C.c_int)]),
     "mc_rsvd_pi": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, _P, _P, _P, C.POINTER(C.c_int)]),
+    "mc_rsvd_basic": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, _P, _P, _P, C.POINTER(C.c_int)]),
     "mc_set_precision": (C.c_int, [_P, C.c_int]),
     "mc_svt_step": (C.c_int, [_P, C.POINTER(McParams), C.POINTER(McIterInfo)]),
     "mc_svt_reset": (C.c_int, [_P]),

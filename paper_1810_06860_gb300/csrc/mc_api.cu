@@ -623,6 +623,28 @@ void power_pi(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id) {
   h->q_real = kb;
 }
 
+// Basis of basic rSVD (Alg. 1, steps 1-7) into h->Q (m x kbp): Q = orth(A
+// Omega), then p times G = orth(A^T Q), Q = orth(A G) -- an orthonormalisation
+// after every product, the cost Alg. 4 halves.
+void power_basic(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id) {
+  const int kbp = (int)round_up(kb, 4);
+  draw_omega(h, kb, kbp, seed, call_id, nullptr, 0, 0);
+  float *Q = fbuf(h, h->Q, (size_t)h->m * kbp);
+  float *H = fbuf(h, h->H, (size_t)h->m * kbp);
+  float *T = fbuf(h, h->T, (size_t)h->n * kbp);
+  float *G = fbuf(h, h->Bt, (size_t)h->n * kbp);
+  spmm_Y(h, h->Om.as<float>(), kbp, kbp, H, kbp);
+  orth_block(h, h->m, kbp, H, kbp, Q, kbp);        // Q = orth(A Omega)
+  for (int i = 0; i < p; ++i) {
+    spmm_Yt(h, Q, kbp, kbp, T, kbp);
+    orth_block(h, h->n, kbp, T, kbp, G, kbp);      // G = orth(A^T Q)
+    spmm_Y(h, G, kbp, kbp, H, kbp);
+    orth_block(h, h->m, kbp, H, kbp, Q, kbp);      // Q = orth(A G)
+  }
+  h->Kq = kbp;
+  h->q_real = kb;
+}
+
 // Steps 8-10 of Alg. 5 with basis Qb (m x Kq): B^T = A^T Qb, G = B B^T,
 // top-kw eigenpairs (values to the host).
 void ritz(mc_handle h, const float *Qb, int ldq, int Kq, int kw, bool fresh_krylov = false) {
@@ -692,13 +714,23 @@ void form_factors(mc_handle h, const float *Qb, int ldq, int ncols, const std::v
 }
 
 // Full rSVD into user buffers.
-mc_status do_rsvd(mc_handle h, bool bki, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U, float *S,
+// algo: 0 rSVD-PI (Alg. 4), 1 rSVD-BKI (Alg. 5), 2 basic rSVD (Alg. 1).
+mc_status do_rsvd(mc_handle h, int algo, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U, float *S,
                   float *V, int *k_out) {
   MC_REQUIRE(k >= 1 && s >= 0, "k must be >= 1 and s >= 0");
-  clamp_kp(h, s, k, p);
+  const bool bki = algo == 1;
+  if (bki) {
+    clamp_kp(h, s, k, p);
+  } else {
+    // one block of k + s columns whatever p (Alg. 1 and 4 keep the width)
+    int p1 = 0;
+    clamp_kp(h, s, k, p1);
+    p = std::max(p, 0);
+  }
   const int kb = k + s;
   if (bki) krylov_bki(h, kb, p, seed, call_id, nullptr, 0, 0);
-  else power_pi(h, kb, p, seed, call_id);
+  else if (algo == 0) power_pi(h, kb, p, seed, call_id);
+  else power_basic(h, kb, p, seed, call_id);
   ritz(h, h->Q.as<float>(), h->Kq, h->Kq, k, bki);
   std::vector<double> sig;
   const int kk = ritz_sigmas(h, k, sig);
@@ -1053,6 +1085,7 @@ mc_status mc_create(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int
     cudaStream_t s = h->stream;
     // row_ptr (int64) -> int32 with checks
     DBuf rp64;
+    BufGuard g_rp64(h->alloc, {&rp64});
     rp64.reserve(h->alloc, sizeof(int64_t) * (m + 1));
     copy_in(s, rp64.p, row_ptr, sizeof(int64_t) * (m + 1));
     h->rp.reserve(h->alloc, sizeof(int) * (m + 1));
@@ -1084,6 +1117,7 @@ mc_status mc_create(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int
     h->perm.reserve(h->alloc, sizeof(int) * std::max<int64_t>(nnz, 1));
     h->yc.reserve(h->alloc, sizeof(float) * std::max<int64_t>(nnz, 1));
     DBuf tmp;
+    BufGuard g_tmp(h->alloc, {&tmp});
     tmp.reserve(h->alloc, csc_tmp_bytes(m, n));
     build_csc(s, m, n, nnz, h->rp.as<int>(), h->ci.as<int>(), h->cp.as<int>(), h->ri.as<int>(), h->perm.as<int>(),
               tmp.p);
@@ -1215,13 +1249,19 @@ mc_status mc_get_values(mc_handle h, float *val) {
 mc_status mc_rsvd_bki(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U, float *S, float *V,
                       int *k_out) {
   if (!h) return MC_EINVAL;
-  return guarded([&]() { return do_rsvd(h, true, k, s, p, seed, call_id, U, S, V, k_out); });
+  return guarded([&]() { return do_rsvd(h, 1, k, s, p, seed, call_id, U, S, V, k_out); });
 }
 
 mc_status mc_rsvd_pi(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U, float *S, float *V,
                      int *k_out) {
   if (!h) return MC_EINVAL;
-  return guarded([&]() { return do_rsvd(h, false, k, s, p, seed, call_id, U, S, V, k_out); });
+  return guarded([&]() { return do_rsvd(h, 0, k, s, p, seed, call_id, U, S, V, k_out); });
+}
+
+mc_status mc_rsvd_basic(mc_handle h, int k, int s, int p, uint64_t seed, uint64_t call_id, float *U, float *S,
+                        float *V, int *k_out) {
+  if (!h) return MC_EINVAL;
+  return guarded([&]() { return do_rsvd(h, 2, k, s, p, seed, call_id, U, S, V, k_out); });
 }
 
 mc_status mc_set_precision(mc_handle h, int precision) {
@@ -1288,6 +1328,7 @@ mc_status mc_svt_sample(mc_handle h, int64_t count, const int64_t *rows, const i
     MC_REQUIRE(h->svt_init, "no SVT estimate yet");
     MC_REQUIRE(rows && cols && out, "null argument");
     DBuf dr, dc, dout;
+    BufGuard g_bufs(h->alloc, {&dr, &dc, &dout});
     dr.reserve(h->alloc, sizeof(int64_t) * count);
     dc.reserve(h->alloc, sizeof(int64_t) * count);
     dout.reserve(h->alloc, sizeof(float) * count);
@@ -1311,6 +1352,7 @@ mc_status mc_spmm(mc_handle h, int trans, int k, const float *X, float *out) {
     const int kp = (int)round_up(k, 4);
     const int64_t rin = trans ? h->m : h->n, rout = trans ? h->n : h->m;
     DBuf dx, dy;
+    BufGuard g_bufs(h->alloc, {&dx, &dy});
     dx.reserve(h->alloc, sizeof(float) * rin * kp);
     dy.reserve(h->alloc, sizeof(float) * rout * kp);
     MC_CUDA(cudaMemsetAsync(dx.p, 0, sizeof(float) * rin * kp, h->stream));

@@ -66,6 +66,22 @@ def test_rsvd_pi_matches_oracle(mc, ratings_small):
     assert metrics.sigma_rel_err(S, So) < SIG_TOL
 
 
+def test_rsvd_basic_matches_oracle(mc, ratings_small):
+    """Basic rSVD (Alg. 1): an orthonormalisation after every product; same
+    Omega, same singular values as the oracle's Alg. 1 (and, by Theorem 1, as
+    rSVD-PI's)."""
+    o = ratings_small
+    with mc.Handle.from_observed(o) as h:
+        U, S, V = h.rsvd_basic(30, s=10, p=3, seed=5, call_id=0)
+        _, Spi, _ = h.rsvd_pi(30, s=10, p=3, seed=5, call_id=0)
+    _, So, Vo = orsvd.rsvd_basic(_A(o), 30, 3, s=10, seed=5, call_id=0)
+    assert metrics.sigma_rel_err(S, So) < SIG_TOL
+    assert metrics.sigma_rel_err(Spi, So) < SIG_TOL
+    gap = np.flatnonzero(np.diff(So) / So[1:] < -0.05)
+    j = int(gap[0]) + 1 if gap.size else 1
+    assert metrics.max_principal_angle(V[:, :j], Vo[:, :j]) < 1e-3
+
+
 def test_rsvd_on_lowrank_exact(mc):
     o = mc_synth.lowrank_uniform(400, 300, 6, frac=1.0, seed=4)  # fully observed rank-6 matrix
     with mc.Handle.from_observed(o) as h:
