@@ -101,8 +101,9 @@ template <int T>
 __global__ void __launch_bounds__(256)
 gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ Y,
                      int ld_y, int64_t rows_per_split, int sym, int same, float *__restrict__ partial, int tiles_j,
-                     int K1p, int K2p) {
+                     int K1p, int K2p, const int *__restrict__ skip) {
   using P = TnSmall<T>;
+  if (skip && *skip) return;  // a pass the previous one made unnecessary
   // output tile (ti, tj) of blockIdx.y; below-diagonal tiles of a Gram are mirrored by the reducer
   const int ti = blockIdx.y / tiles_j, tj = blockIdx.y % tiles_j;
   if (sym && tj < ti) return;
@@ -188,8 +189,9 @@ gemm_tn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
 // outputs with 8 lanes of split groups each, then adds the 8 group sums in order.
 __global__ void __launch_bounds__(256)
 gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ partial, int K1p, int K2p, bool sym,
-                      int mirror, float *__restrict__ C, int ld_c) {
+                      int mirror, float *__restrict__ C, int ld_c, const int *__restrict__ skip = nullptr) {
   __shared__ float sh[8][33];
+  if (skip && *skip) return;
   const int64_t total = (int64_t)K1 * K2;
   const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int64_t tile = (int64_t)K1p * K2p;
@@ -312,8 +314,11 @@ template <int KM1>
 __global__ void __launch_bounds__(256)
 gemm_nn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x, const float *__restrict__ W,
                      int ld_w, const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z,
-                     int ld_z, int64_t chunks_per_block) {
+                     int ld_z, int64_t chunks_per_block, const int *__restrict__ copy_if) {
   using P = NnSmall<KM1>;
+  // copy mode (the factor is the identity: a pass the previous one made
+  // unnecessary): Z = X, read through the same staging
+  const bool copy = copy_if && *copy_if;
   extern __shared__ __align__(16) float nns[];
   float *ws = nns;                   // [KM1][64]
   float *xs = nns + KM1 * 64;        // [STAGES][BM][LDX]
@@ -358,7 +363,13 @@ gemm_nn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
     const float *xb = xs + (size_t)(c % P::STAGES) * NNS_BM * P::LDX;
     float acc[4][4] = {};
     if (j0 + tx * 4 < K2) {
-      for (int k4 = 0; k4 < K4; ++k4) {
+      if (copy) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = xb[(ty * 4 + u) * P::LDX + j0 + tx * 4 + v];
+      }
+      for (int k4 = 0; k4 < (copy ? 0 : K4); ++k4) {
         float4 a[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) a[u] = *reinterpret_cast<const float4 *>(xb + (ty * 4 + u) * P::LDX + k4 * 4);
@@ -382,7 +393,11 @@ gemm_nn_small_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int
         const int64_t r = rb + ty * 4 + u;
         if (r >= R) continue;
         float *z = Z + r * ld_z + j0 + tx * 4;
-        if (vec_out) {
+        if (copy) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (j0 + tx * 4 + v < K2) z[v] = acc[u][v];
+        } else if (vec_out) {
           float4 o = make_float4(acc[u][0] * sc[0], acc[u][1] * sc[1], acc[u][2] * sc[2], acc[u][3] * sc[3]);
           if (beta != 0.f) {
             const float4 pz = *reinterpret_cast<const float4 *>(z);
@@ -486,8 +501,10 @@ gemm_nn_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x,
 // next step can be read right after the second barrier.
 __global__ void __launch_bounds__(1024)
 chol_inv_small_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
-                      float ref_tol, float *__restrict__ Rinv) {
+                      float ref_tol, float *__restrict__ Rinv, const int *__restrict__ skip_if,
+                      int *__restrict__ set_skip) {
   extern __shared__ float sh[];
+  if (skip_if && *skip_if) return;  // a pass the previous one made unnecessary
   const int ls = (K % 2 == 0) ? K + 1 : K;  // odd row stride: column reads are conflict-free
   float *L = sh;                            // K x ls
   float *B = L + (size_t)K * ls;            // K x ls
@@ -516,11 +533,24 @@ chol_inv_small_kernel(int K, const float *__restrict__ G, int ld, float shift_re
   __syncthreads();
   const float shift = shift_rel * s_tr / K;
   const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
+  float dev = 0.f;  // largest |G - I| over the lower triangle
   for (int t = tid; t < K * K; t += nt) {
     const int i = t / K, j = t % K;
     const bool live = flags[i] != 0.f && flags[j] != 0.f;
-    L[i * ls + j] = (j <= i && live) ? G[(int64_t)i * ld + j] + (i == j ? shift : 0.f) : 0.f;
+    const float g = j <= i ? G[(int64_t)i * ld + j] : 0.f;
+    if (j <= i) dev = fmaxf(dev, fabsf(g - (i == j ? 1.f : 0.f)));
+    L[i * ls + j] = (j <= i && live) ? g + (i == j ? shift : 0.f) : 0.f;
     B[i * ls + j] = (i == j) ? 1.f : 0.f;
+  }
+  if (set_skip) {
+    __shared__ unsigned s_dev;
+    if (tid == 0) s_dev = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, off));
+    if (lane == 0) atomicMax(&s_dev, __float_as_uint(dev));  // nonnegative floats order as their bits
+    __syncthreads();
+    if (tid == 0) *set_skip = __uint_as_float(s_dev) < 1e-2f ? 1 : 0;
   }
   __syncthreads();
   for (int j = 0; j < K; ++j) {
@@ -1117,7 +1147,7 @@ size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2) {
 
 template <int T>
 static void launch_tn_small(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y,
-                            int ld_y, bool symg, bool same, float *partial, const TnPlan &pl) {
+                            int ld_y, bool symg, bool same, float *partial, const TnPlan &pl, const int *skip) {
   const size_t smem = TnSmall<T>::smem_bytes(same && pl.tiles_i * pl.tiles_j == 1);
   // the attribute is per kernel and process-wide: always set the largest size
   // any call needs, so concurrent callers on other threads never lower it
@@ -1125,12 +1155,12 @@ static void launch_tn_small(cudaStream_t st, int64_t R, int K1, int K2, const fl
                                (int)TnSmall<T>::smem_bytes(false)));
   dim3 grid((unsigned)pl.nsplit, (unsigned)(pl.tiles_i * pl.tiles_j));
   gemm_tn_small_kernel<T><<<grid, 256, smem, st>>>(R, K1, K2, X, ld_x, Y, ld_y, pl.rps, symg ? 1 : 0, same ? 1 : 0,
-                                                   partial, pl.tiles_j, pl.K1p, pl.K2p);
+                                                   partial, pl.tiles_j, pl.K1p, pl.K2p, skip);
   MC_CHECK_LAUNCH();
 }
 
 void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y, int ld_y, float *C,
-             int ld_c, bool sym, float *partial) {
+             int ld_c, bool sym, float *partial, const int *skip) {
   if (K1 <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0 && ld_y % 4 == 0, "gemm_tn: leading dims must be multiples of 4");
   MC_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0,
@@ -1138,18 +1168,20 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
   const bool same = (X == Y && ld_x == ld_y && K1 == K2);
   const bool symg = sym && same;  // only a true Gram skips the lower tiles
   const TnPlan pl = tn_plan(R, K1, K2, symg);
-  if (pl.T == 16) launch_tn_small<16>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl);
-  else if (pl.T == 32) launch_tn_small<32>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl);
-  else launch_tn_small<64>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl);
+  if (pl.T == 16) launch_tn_small<16>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl, skip);
+  else if (pl.T == 32) launch_tn_small<32>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl, skip);
+  else launch_tn_small<64>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl, skip);
   const int64_t total = (int64_t)K1 * K2;
   const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
-  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, pl.nsplit, partial, pl.K1p, pl.K2p, symg, 4, C, ld_c);
+  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, pl.nsplit, partial, pl.K1p, pl.K2p, symg, 4, C, ld_c, skip);
   MC_CHECK_LAUNCH();
 }
 
 void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W, int ld_w,
-             const float *colscale, float alpha, float beta, float *Z, int ld_z) {
+             const float *colscale, float alpha, float beta, float *Z, int ld_z, const int *copy_if) {
   if (R <= 0 || K2 <= 0) return;
+  MC_REQUIRE(!copy_if || (K1 == K2 && K2 > 16 && K1 <= 64 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0),
+             "gemm_nn: the copy mode needs the small-factor kernel (16 < K1 == K2 <= 64, X 16-byte aligned)");
   MC_REQUIRE(ld_x % 4 == 0, "gemm_nn: ld_x must be a multiple of 4");
   // narrow outputs: a thread per row (the 64-column tiles would leave most threads idle)
   if (K2 <= 16 && K1 <= 1024) {
@@ -1181,7 +1213,7 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
   MC_CUDA(cudaFuncSetAttribute(gemm_nn_small_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
                                (int)NnSmall<KM>::smem));                                                             \
   gemm_nn_small_kernel<KM><<<grid, 256, NnSmall<KM>::smem, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, \
-                                                                 Z, ld_z, per)
+                                                                 Z, ld_z, per, copy_if)
     MC_NN_SMALL(64);
 #undef MC_NN_SMALL
     MC_CHECK_LAUNCH();
@@ -1193,7 +1225,7 @@ void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
 }
 
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag, float ref_tol,
-              float *Rinv) {
+              float *Rinv, const int *skip_if, int *set_skip) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
   if (K <= 128) {
     const int ls = (K % 2 == 0) ? K + 1 : K;
@@ -1201,10 +1233,11 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
     constexpr size_t kMax = sizeof(float) * (2 * 128 * 129 + 128);  // K = 128; fixed for concurrent callers
     MC_CUDA(cudaFuncSetAttribute(chol_inv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax));
     const int threads = K <= 32 ? 256 : (K <= 64 ? 512 : 1024);
-    chol_inv_small_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv);
+    chol_inv_small_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip);
     MC_CHECK_LAUNCH();
     return;
   }
+  MC_REQUIRE(!skip_if && !set_skip, "chol_inv: the pass flags need K <= 128");
   const size_t base = sizeof(float) * ((size_t)K * K + K);
   MC_REQUIRE(base <= 220 * 1024, "chol_inv: block too wide for shared memory");
   const bool x_sm = base + sizeof(float) * (size_t)K * K <= 220 * 1024;

@@ -29,6 +29,8 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <cstdlib>
+#include <cstring>
 
 namespace mc {
 namespace {
@@ -312,6 +314,241 @@ eig_tridiag_mid_kernel(int K, const float *__restrict__ A, int lda, float *__res
       g_beta[K - 2] = 0.f;
     }
     g_d[K - 1] = P[pk(K - 1, K - 1)];
+    g_e[K - 1] = 0.f;
+    g_beta[K - 1] = 0.f;
+  }
+}
+
+// Householder tridiagonalisation for 64 < K <= 256 with the lower triangle in
+// registers (the fastest variant for this range).  512 threads: lane l holds
+// the rows r = l + 32 a (a < 8), warp w the columns c = w + 16 b (b < 16);
+// element (r, c) is kept when r >= c (at most 72 registers; the others hold
+// zero).  Step j: the warp holding column j forms the reflector (warp
+// reductions) and publishes v.  Every thread adds its elements' terms of
+// p = beta A v twice over for the symmetric matrix: A(r, c) v(c) to row r
+// (summed across the warps through shared memory) and, for r > c, A(r, c) v(r)
+// to column c (summed across the lanes of the warp by a shuffle reduce-
+// scatter).  A thread per row finishes p and the dot v.p, and every thread
+// applies A -= v w^T + w v^T to its elements.  Three barriers per step; only
+// columns of the trailing block (c > j) are visited, a warp-uniform test.
+// Outputs (d, e, beta, reflectors in Hv) as eig_tridiag_kernel.
+constexpr int TR_K = 256, TR_THREADS = 512, TR_NW = TR_THREADS / 32;
+constexpr int TR_A = 8, TR_B = 16;
+
+// x[a][b] (column b of this thread's block) for a compile-time b
+template <int B>
+__device__ __forceinline__ void tr_col(const float (&x)[TR_A][TR_B], float (&col)[TR_A]) {
+#pragma unroll
+  for (int a = 0; a < TR_A; ++a) col[a] = (B <= 2 * a + 1) ? x[a][B] : 0.f;
+}
+
+__global__ void __launch_bounds__(TR_THREADS, 1)
+eig_tridiag_reg_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d,
+                       float *__restrict__ g_e, float *__restrict__ g_beta, float *__restrict__ Hv) {
+  __shared__ float vs[2][TR_K], ps[2][TR_K], colp[TR_K];
+  __shared__ float part[TR_NW][TR_K];
+  __shared__ float dotp[2][TR_K / 32];
+  __shared__ float s_beta[2], s_amax[TR_NW];
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const unsigned full = 0xffffffffu;
+  for (int i = tid; i < TR_K; i += TR_THREADS) {
+    vs[0][i] = 0.f;
+    vs[1][i] = 0.f;
+    ps[0][i] = 0.f;
+    ps[1][i] = 0.f;
+    colp[i] = 0.f;
+  }
+  // stored(a, b): b < 2a always; b == 2a when l >= w; b == 2a + 1 when l >= w + 16
+  float x[TR_A][TR_B];
+  float amax = 0.f;
+#pragma unroll
+  for (int a = 0; a < TR_A; ++a) {
+#pragma unroll
+    for (int b = 0; b < TR_B; ++b) {
+      x[a][b] = 0.f;
+      if (b > 2 * a + 1) continue;
+      const int r = l + 32 * a, c = w + 16 * b;
+      const bool keep = b < 2 * a || (b == 2 * a ? l >= w : l >= w + 16);
+      if (keep && r < K && c < K) x[a][b] = A[(int64_t)r * lda + c];
+      amax = fmaxf(amax, fabsf(x[a][b]));
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(full, amax, off));
+  if (l == 0) s_amax[w] = amax;
+  __syncthreads();
+  amax = 0.f;
+#pragma unroll
+  for (int q = 0; q < TR_NW; ++q) amax = fmaxf(amax, s_amax[q]);
+  const float sig_floor = fmaxf((FLT_EPSILON * amax) * (FLT_EPSILON * amax), 1e-37f);
+
+  int buf = 0;
+  for (int j = 0; j + 2 < K; ++j, buf ^= 1) {
+    if (w == (j & 15)) {
+      // column j (rows r = l + 32 a; zero where not stored, i.e. above the diagonal)
+      float col[TR_A];
+      switch (j >> 4) {
+        case 0: tr_col<0>(x, col); break;
+        case 1: tr_col<1>(x, col); break;
+        case 2: tr_col<2>(x, col); break;
+        case 3: tr_col<3>(x, col); break;
+        case 4: tr_col<4>(x, col); break;
+        case 5: tr_col<5>(x, col); break;
+        case 6: tr_col<6>(x, col); break;
+        case 7: tr_col<7>(x, col); break;
+        case 8: tr_col<8>(x, col); break;
+        case 9: tr_col<9>(x, col); break;
+        case 10: tr_col<10>(x, col); break;
+        case 11: tr_col<11>(x, col); break;
+        case 12: tr_col<12>(x, col); break;
+        case 13: tr_col<13>(x, col); break;
+        case 14: tr_col<14>(x, col); break;
+        default: tr_col<15>(x, col); break;
+      }
+      float sq = 0.f, mine_d = 0.f, mine_x0 = 0.f;
+#pragma unroll
+      for (int a = 0; a < TR_A; ++a) {
+        const int r = l + 32 * a;
+        if (r > j + 1) sq = fmaf(col[a], col[a], sq);
+        if (a == (j >> 5)) mine_d = col[a];
+        if (a == ((j + 1) >> 5)) mine_x0 = col[a];
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(full, sq, off);
+      const float dj = __shfl_sync(full, mine_d, j & 31);
+      const float x0 = __shfl_sync(full, mine_x0, (j + 1) & 31);
+      float bt = 0.f, alpha = x0, v0 = 0.f;
+      if (sq > sig_floor) {
+        const float mu = sqrtf(x0 * x0 + sq);
+        alpha = x0 <= 0.f ? mu : -mu;
+        v0 = x0 - alpha;
+        bt = 2.0f / (v0 * v0 + sq);
+      }
+#pragma unroll
+      for (int a = 0; a < TR_A; ++a) {
+        const int r = l + 32 * a;
+        if (r > j && r < K) {
+          const float v = r == j + 1 ? v0 : col[a];
+          vs[buf][r] = v;
+          Hv[(int64_t)j * K + (r - j - 1)] = v;
+        }
+      }
+      if (l == 0) {
+        g_d[j] = dj;
+        g_e[j] = alpha;
+        g_beta[j] = bt;
+        s_beta[buf] = bt;
+      }
+    }
+    __syncthreads();
+    const float bt = s_beta[buf];
+    if (bt == 0.f) continue;  // uniform
+    float vr[TR_A];
+#pragma unroll
+    for (int a = 0; a < TR_A; ++a) vr[a] = vs[buf][l + 32 * a];
+    // ---- p = beta A v: row terms (rp) and transposed column terms (cp) ----
+    float rp[TR_A], cp[TR_B];
+#pragma unroll
+    for (int a = 0; a < TR_A; ++a) rp[a] = 0.f;
+#pragma unroll
+    for (int b = 0; b < TR_B; ++b) {
+      cp[b] = 0.f;
+      const int c = w + 16 * b;
+      if (c > j && c < K) {
+        const float vc = vs[buf][c];
+#pragma unroll
+        for (int a = 0; a < TR_A; ++a) {
+          if (b > 2 * a + 1) continue;
+          const float e = x[a][b];
+          rp[a] = fmaf(e, vc, rp[a]);
+          // the diagonal element (r == c) contributes once, to its row
+          const bool diag = (b == 2 * a && l == w) || (b == 2 * a + 1 && l == w + 16);
+          if (!diag) cp[b] = fmaf(e, vr[a], cp[b]);
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < TR_A; ++a) part[w][l + 32 * a] = rp[a];
+    {
+      // reduce-scatter of the 16 column sums over the 32 lanes: after the
+      // levels on lane bits 4..1, lane l holds column b = l >> 1 (both lanes of a pair)
+      float t8[8], t4[4], t2[2];
+      const bool h4 = l & 16, h3 = l & 8, h2 = l & 4, h1 = l & 2;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float keep = h4 ? cp[i + 8] : cp[i], send = h4 ? cp[i] : cp[i + 8];
+        t8[i] = keep + __shfl_xor_sync(full, send, 16);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float keep = h3 ? t8[i + 4] : t8[i], send = h3 ? t8[i] : t8[i + 4];
+        t4[i] = keep + __shfl_xor_sync(full, send, 8);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = h2 ? t4[i + 2] : t4[i], send = h2 ? t4[i] : t4[i + 2];
+        t2[i] = keep + __shfl_xor_sync(full, send, 4);
+      }
+      const float keep = h1 ? t2[1] : t2[0], send = h1 ? t2[0] : t2[1];
+      float t1 = keep + __shfl_xor_sync(full, send, 2);
+      t1 += __shfl_xor_sync(full, t1, 1);
+      const int c = w + 16 * (l >> 1);
+      if ((l & 1) == 0 && c > j && c < K) colp[c] = t1;
+    }
+    __syncthreads();
+    if (tid < TR_K) {
+      const int r = tid;
+      float pr = 0.f;
+      if (r > j && r < K) {
+        float s = colp[r];
+#pragma unroll
+        for (int q = 0; q < TR_NW; ++q) s += part[q][r];
+        pr = bt * s;
+        ps[buf][r] = pr;
+      }
+      float dv = pr * vs[buf][r];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) dv += __shfl_xor_sync(full, dv, off);
+      if (l == 0) dotp[buf][tid >> 5] = dv;
+    }
+    __syncthreads();
+    float dot = 0.f;
+#pragma unroll
+    for (int q = 0; q < TR_K / 32; ++q) dot += dotp[buf][q];
+    const float cc = 0.5f * bt * dot;
+    // ---- A -= v w^T + w v^T with w = p - c v ----
+    float wr[TR_A];
+#pragma unroll
+    for (int a = 0; a < TR_A; ++a) wr[a] = ps[buf][l + 32 * a] - cc * vr[a];
+#pragma unroll
+    for (int b = 0; b < TR_B; ++b) {
+      const int c = w + 16 * b;
+      if (c > j && c < K) {
+        const float vc = vs[buf][c], wc = ps[buf][c] - cc * vc;
+#pragma unroll
+        for (int a = 0; a < TR_A; ++a) {
+          if (b > 2 * a + 1) continue;
+          const bool keep = b < 2 * a || (b == 2 * a ? l >= w : l >= w + 16);
+          if (keep) x[a][b] -= vr[a] * wc + wr[a] * vc;
+        }
+      }
+    }
+  }
+  // the last 2 x 2 block: each of its three elements is written by its owner
+#pragma unroll
+  for (int a = 0; a < TR_A; ++a) {
+#pragma unroll
+    for (int b = 0; b < TR_B; ++b) {
+      if (b > 2 * a + 1) continue;
+      const int r = l + 32 * a, c = w + 16 * b;
+      if (r >= K || c >= K || r < c) continue;
+      if (r == K - 2 && c == K - 2) g_d[K - 2] = x[a][b];
+      if (r == K - 1 && c == K - 2) g_e[K - 2] = x[a][b];
+      if (r == K - 1 && c == K - 1) g_d[K - 1] = x[a][b];
+    }
+  }
+  if (tid == 0) {
+    g_beta[K - 2] = 0.f;
     g_e[K - 1] = 0.f;
     g_beta[K - 1] = 0.f;
   }
@@ -1128,7 +1365,261 @@ eig_backtr_kernel(int K, const float *__restrict__ g_beta, const float *__restri
   for (int a = tid; a < K; a += BT_THREADS) W[(int64_t)a * ld_w + t] = z[a];
 }
 
+// ---- per-eigenvalue stages for 64 < K <= 256 --------------------------------
+// Multisection for eigenvalue blockIdx.x (the t-th largest): one warp, 32
+// Sturm counts per round (a lane per point) shrink the bracket 33-fold, from
+// the Gershgorin interval to 2 ulp; the same counts and bracket rule as the
+// one-CTA multisection.
+__global__ void __launch_bounds__(32)
+eig_bisect_kernel(int K, int kw, const float *__restrict__ g_d, const float *__restrict__ g_e,
+                  float *__restrict__ lam_out) {
+  __shared__ float d[TR_K], e2[TR_K];
+  const int lane = threadIdx.x, t = blockIdx.x;
+  const unsigned full = 0xffffffffu;
+  float glo = FLT_MAX, ghi = -FLT_MAX, emax = 0.f;
+  for (int a = lane; a < K; a += 32) {
+    const float ea = a + 1 < K ? g_e[a] : 0.f, eb = a > 0 ? g_e[a - 1] : 0.f;
+    d[a] = g_d[a];
+    e2[a] = ea * ea;
+    const float r = fabsf(eb) + fabsf(ea);
+    glo = fminf(glo, d[a] - r);
+    ghi = fmaxf(ghi, d[a] + r);
+    emax = fmaxf(emax, ea * ea);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    glo = fminf(glo, __shfl_xor_sync(full, glo, off));
+    ghi = fmaxf(ghi, __shfl_xor_sync(full, ghi, off));
+    emax = fmaxf(emax, __shfl_xor_sync(full, emax, off));
+  }
+  __syncwarp();
+  const float span = fmaxf(ghi - glo, fmaxf(fabsf(glo), fabsf(ghi)) * 1e-6f) + 1e-30f;
+  float lo = glo - 1e-3f * span, hi = ghi + 1e-3f * span;
+  const float pivmin = FLT_MIN * fmaxf(1.0f, emax);
+  const int target = K - 1 - t;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;  // uniform
+    const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
+    float qq = d[0] - x;
+    int cnt = qq < 0.f;
+    for (int a = 1; a < K; ++a) {
+      if (fabsf(qq) < pivmin) qq = -pivmin;
+      qq = d[a] - x - __fdividef(e2[a - 1], qq);
+      cnt += qq < 0.f;
+    }
+    const unsigned below = __ballot_sync(full, cnt <= target);
+    const unsigned above = __ballot_sync(full, cnt > target);
+    const float xb = __shfl_sync(full, x, below ? 31 - __clz(below) : 0);
+    const float xa = __shfl_sync(full, x, above ? __ffs(above) - 1 : 0);
+    const float nl = below ? fmaxf(lo, xb) : lo;
+    const float nh = above ? fminf(hi, xa) : hi;
+    lo = nl;
+    hi = fmaxf(nl, nh);
+  }
+  if (lane == 0) lam_out[t] = 0.5f * (lo + hi);
+}
+
+// Orthonormalisation of the inverse-iteration vectors Z (K x kw, kw <= 64):
+// three CholeskyQR passes in shared memory (the first with a relative shift
+// of 1e-6 of the mean diagonal), each Z <- Z R^{-1} with Z^T Z (+ shift) =
+// R^T R.  Equal eigenvalues aside, the columns are already nearly orthogonal,
+// so the Gram is well conditioned; a column whose pivot falls to the noise
+// floor is zeroed.  256 threads: the Gram as eight warp partials (a warp per
+// eighth of the rows, lanes along columns), the Cholesky factor by the
+// block, the solve a thread per row.
+constexpr int EO_THREADS = 256, EO_KW = 64;
+__global__ void __launch_bounds__(EO_THREADS, 1)
+eig_orth_kernel(int K, int kw, float *__restrict__ Z, int ldz) {
+  extern __shared__ __align__(16) float eo[];
+  const int lz = kw | 1;                       // odd row stride
+  float *Zs = eo;                              // K x lz
+  float *P = Zs + (size_t)K * lz;              // 8 x kw x kw warp partials
+  float *G = P + (size_t)8 * kw * kw;          // kw x (kw + 1)
+  __shared__ float s_drop, s_pivok[EO_KW], rdg[EO_KW];
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int lg = kw + 1;
+  for (int f = tid; f < K * kw; f += EO_THREADS) {
+    const int a = f / kw, c = f % kw;
+    Zs[a * lz + c] = Z[(int64_t)a * ldz + c];
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 3; ++pass) {
+    // partial Grams: warp wid over rows a = wid, wid + 8, ...; lane i (and i + 32)
+    for (int j0 = 0; j0 < kw; j0 += 16) {
+      float acc0[16], acc1[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc0[q] = acc1[q] = 0.f;
+      for (int a = wid; a < K; a += 8) {
+        const float *zr = Zs + a * lz;
+        const float z0 = lane < kw ? zr[lane] : 0.f, z1 = lane + 32 < kw ? zr[lane + 32] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float zj = j0 + q < kw ? zr[j0 + q] : 0.f;
+          acc0[q] = fmaf(z0, zj, acc0[q]);
+          acc1[q] = fmaf(z1, zj, acc1[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (j0 + q >= kw) break;
+        if (lane < kw) P[((size_t)wid * kw + lane) * kw + j0 + q] = acc0[q];
+        if (lane + 32 < kw) P[((size_t)wid * kw + lane + 32) * kw + j0 + q] = acc1[q];
+      }
+    }
+    __syncthreads();
+    for (int f = tid; f < kw * kw; f += EO_THREADS) {
+      const int i = f / kw, j = f % kw;
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += P[((size_t)q * kw + i) * kw + j];
+      G[i * lg + j] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float tr = 0.f, mx = 0.f;
+      for (int i = 0; i < kw; ++i) {
+        tr += G[i * lg + i];
+        mx = fmaxf(mx, G[i * lg + i]);
+      }
+      const float shift = pass == 0 ? 1e-6f * tr / (float)kw : 0.f;
+      for (int i = 0; i < kw; ++i) G[i * lg + i] += shift;
+      s_drop = fmaxf(1e-30f, 1e-12f * mx) + shift;
+    }
+    __syncthreads();
+    // right-looking Cholesky G = R^T R in place: the strict upper triangle
+    // holds R, its diagonal goes to rdg (G's diagonal is not rewritten, so the
+    // pivot read and the row scaling need no barrier between them); warps
+    // take the rows of the trailing update, lanes its columns
+    for (int j = 0; j < kw; ++j) {
+      const float piv = G[j * lg + j];
+      const bool ok = piv > s_drop;
+      const float inv = ok ? rsqrtf(piv) : 0.f;
+      for (int c = j + 1 + tid; c < kw; c += EO_THREADS) G[j * lg + c] *= inv;
+      if (tid == 0) {
+        rdg[j] = ok ? piv * inv : 0.f;
+        s_pivok[j] = ok ? 1.f : 0.f;
+      }
+      __syncthreads();
+      for (int r = j + 1 + wid; r < kw; r += EO_THREADS / 32) {
+        const float grj = G[j * lg + r];
+        for (int c = r + lane; c < kw; c += 32) G[r * lg + c] = fmaf(-grj, G[j * lg + c], G[r * lg + c]);
+      }
+      __syncthreads();
+    }
+    // rows of Z: x R = z  (x_c = (z_c - sum_{k<c} x_k R[k][c]) / R[c][c]); dropped columns are zero
+    for (int a = tid; a < K; a += EO_THREADS) {
+      float *zr = Zs + a * lz;
+      for (int c = 0; c < kw; ++c) {
+        float s0 = zr[c], s1 = 0.f;
+        int k = 0;
+        for (; k + 1 < c; k += 2) {
+          s0 = fmaf(-zr[k], G[k * lg + c], s0);
+          s1 = fmaf(-zr[k + 1], G[(k + 1) * lg + c], s1);
+        }
+        if (k < c) s0 = fmaf(-zr[k], G[k * lg + c], s0);
+        zr[c] = s_pivok[c] != 0.f ? (s0 + s1) / rdg[c] : 0.f;
+      }
+    }
+    __syncthreads();
+  }
+  for (int f = tid; f < K * kw; f += EO_THREADS) {
+    const int a = f / kw, c = f % kw;
+    Z[(int64_t)a * ldz + c] = Zs[a * lz + c];
+  }
+}
+
+size_t eig_orth_smem(int K, int kw) {
+  return sizeof(float) * ((size_t)K * (kw | 1) + (size_t)8 * kw * kw + (size_t)kw * (kw + 1));
+}
+
+// Back-transformation W = H_0 H_1 ... H_{K-3} Z, a warp per vector: the
+// vector lives in registers (K <= 256: 8 entries per lane), the reflectors of
+// a chunk are staged in shared memory once for the CTA's eight warps, and each
+// reflector costs the warp a dot product (shuffle reduction) and an update,
+// without block barriers.
+constexpr int BW_THREADS = 256, BW_CHUNK = 16;
+__global__ void __launch_bounds__(BW_THREADS)
+eig_backtr_warp_kernel(int K, int kw, const float *__restrict__ g_beta, const float *__restrict__ Hv,
+                       const float *__restrict__ Z, int ldz, float *__restrict__ W, int ld_w) {
+  __shared__ __align__(16) float hv[BW_CHUNK][TR_K];
+  __shared__ float bt[BW_CHUNK];
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int t = blockIdx.x * (BW_THREADS / 32) + wid;
+  const bool live = t < kw;
+  const unsigned full = 0xffffffffu;
+  float z[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int a = lane + 32 * q;
+    z[q] = live && a < K ? Z[(int64_t)a * ldz + t] : 0.f;
+  }
+  for (int top = K - 3; top >= 0; top -= BW_CHUNK) {
+    const int lowi = max(0, top - BW_CHUNK + 1);
+    __syncthreads();
+    // row i of the chunk: the reflector of step i aligned to global rows (zero at rows <= i)
+    for (int f = tid; f < (top - lowi + 1) * TR_K; f += BW_THREADS) {
+      const int r = f / TR_K, a = f % TR_K, i = lowi + r;
+      hv[r][a] = (a > i && a < K) ? Hv[(int64_t)i * K + (a - i - 1)] : 0.f;
+    }
+    if (tid <= top - lowi) bt[tid] = g_beta[lowi + tid];
+    __syncthreads();
+    if (live) {
+      for (int i = top; i >= lowi; --i) {
+        const float b = bt[i - lowi];
+        if (b == 0.f) continue;
+        const float *v = hv[i - lowi];
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc = fmaf(v[lane + 32 * q], z[q], acc);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(full, acc, off);
+        const float h = b * acc;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) z[q] = fmaf(-v[lane + 32 * q], h, z[q]);
+      }
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int a = lane + 32 * q;
+      if (a < K) W[(int64_t)a * ld_w + t] = z[q];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ plans --
+// MC_EIG_TRI=packed keeps the packed shared-memory reduction for 64 < K <= 256.
+bool tri_reg_on() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_EIG_TRI");
+    return !(v && std::strcmp(v, "packed") == 0);
+  }();
+  return on;
+}
+
+// 64 < K <= 256 with at most 64 wanted pairs: multisection, inverse
+// iteration and back-transformation on a CTA or warp per eigenvalue, the
+// CholeskyQR orthonormalisation in one CTA (MC_EIG_MANY=0 keeps the one-CTA
+// stages).
+bool eig_many_cta(int K, int kw) {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_EIG_MANY");
+    return !(v && v[0] == '0');
+  }();
+  return on && K > TS_K && K <= TR_K && kw <= EO_KW;
+}
+
+// Matrices wider than this run the per-eigenvalue stages on many CTAs
+// (MC_EIG_SPLIT_K overrides).
+int split_k() {
+  static const int v = [] {
+    const char *e = std::getenv("MC_EIG_SPLIT_K");
+    return e ? std::max(1, std::atoi(e)) : SPLIT_K;
+  }();
+  return v;
+}
+
 struct EigPlan {
   int coop;          // many-CTA reduction (K > 256, cooperative launch available)
   int64_t g_af, g_pv, g_part;
@@ -1179,7 +1670,7 @@ EigPlan eig_plan(int K, int kw) {
   off += pl.coop ? 1024 : 0;
   VecLayout vl{};
   vl.ldz = kw | 1;
-  const bool split = K > SPLIT_K;
+  const bool split = K > split_k() || eig_many_cta(K, kw);
   const size_t vfixed =
       sizeof(float) * (3 * (size_t)K + 4 * (size_t)kw + NW * 32 + (size_t)HV_CHUNK * K + 2 * HV_CHUNK * HV_CHUNK +
                        (size_t)HV_CHUNK * kw) + 16;
@@ -1238,6 +1729,9 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   } else if (K <= TS_K) {
     eig_tridiag_small_kernel<<<1, TS_THREADS, 0, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                        gw + pl.g_hv);
+  } else if (K <= TR_K && tri_reg_on()) {
+    eig_tridiag_reg_kernel<<<1, TR_THREADS, 0, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
+                                                     gw + pl.g_hv);
   } else if (K <= TM_K) {
     const size_t smem = sizeof(float) * ((size_t)K * (K + 1) / 2);
     MC_CUDA(cudaFuncSetAttribute(eig_tridiag_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1256,7 +1750,24 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   }
 #undef MC_TRI_ARGS
   MC_CHECK_LAUNCH();
-  if (K <= SPLIT_K) {
+  if (eig_many_cta(K, kw)) {
+    float *Zg = gw + pl.vl.g_z;
+    eig_bisect_kernel<<<kw, 32, 0, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam);
+    MC_CHECK_LAUNCH();
+    const size_t ism = sizeof(float) * 7 * (size_t)K;
+    MC_CUDA(cudaFuncSetAttribute(eig_invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(7 * 4 * 1024)));
+    eig_invit_kernel<<<kw, 32, ism, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam, Zg, pl.vl.ldz);
+    MC_CHECK_LAUNCH();
+    const size_t osm = eig_orth_smem(K, kw);
+    MC_CUDA(cudaFuncSetAttribute(eig_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_orth_smem(TR_K, EO_KW)));
+    eig_orth_kernel<<<1, EO_THREADS, osm, st>>>(K, kw, Zg, pl.vl.ldz);
+    MC_CHECK_LAUNCH();
+    eig_backtr_warp_kernel<<<(kw + BW_THREADS / 32 - 1) / (BW_THREADS / 32), BW_THREADS, 0, st>>>(
+        K, kw, gw + pl.g_beta, gw + pl.g_hv, Zg, pl.vl.ldz, W, ld_w);
+    MC_CHECK_LAUNCH();
+    return;
+  }
+  if (K <= split_k()) {
     // small matrices: 256 threads (cheaper barriers; 64 measured slower), else 1024
     if (K <= SMALL_K)
       eig_vectors_kernel<256><<<1, 256, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,

@@ -469,41 +469,51 @@ int tc_min_k() {
   return v;
 }
 
-void gram(mc_handle h, int64_t R, int K, const float *X, int ld, float *Gout, int ldg) {
+void gram(mc_handle h, int64_t R, int K, const float *X, int ld, float *Gout, int ldg, const int *skip = nullptr) {
   Scope sc(h, MC_T_GRAM, 4.0 * R * K + 4.0 * K * K, 1.0 * R * K * (K + 1));
-  if (use_tensor_gram() && K >= tc_min_k() && gram_tc_supported(K, ld, X)) {
+  if (!skip && use_tensor_gram() && K >= tc_min_k() && gram_tc_supported(K, ld, X)) {
     fbuf(h, h->tn_part, gram_tc_scratch_floats(R, K));
     gram_tc(h->stream, R, K, X, ld, Gout, ldg, h->tn_part.as<float>(), h->flags.as<int>() + 3);
     return;
   }
   fbuf(h, h->tn_part, gemm_tn_scratch_floats(R, K, K));
-  gemm_tn(h->stream, R, K, K, X, ld, X, ld, Gout, ldg, true, h->tn_part.as<float>());
+  gemm_tn(h->stream, R, K, K, X, ld, X, ld, Gout, ldg, true, h->tn_part.as<float>(), skip);
 }
 
 // One CholeskyQR pass: out = X R^{-1} with X^T X + shift I = R^T R.
+// set_skip: device flag set when this pass's Gram is within 1e-2 of I;
+// skip_if: device flag that turns this pass into out = X (its Gram, factor
+// and product are not computed).
 void cholqr_pass(mc_handle h, int64_t R, int K, const float *X, int ldx, float *out, int ldo, float shift_rel,
-                 const float *ref_diag = nullptr) {
+                 const float *ref_diag = nullptr, int *set_skip = nullptr, const int *skip_if = nullptr) {
   float *G = fbuf(h, h->G, (size_t)K * K);
-  gram(h, R, K, X, ldx, G, K);
+  gram(h, R, K, X, ldx, G, K, skip_if);
   float *Ri = fbuf(h, h->Rinv, (size_t)K * K);
   {
     // a column keeping less than 1e-5 of its norm through the projection is noise
     Scope sc(h, MC_T_SMALL);
-    chol_inv(h->stream, K, G, K, shift_rel, ref_diag, 1e-10f, Ri);
+    chol_inv(h->stream, K, G, K, shift_rel, ref_diag, 1e-10f, Ri, skip_if, set_skip);
   }
   Scope sc(h, MC_T_GEMM, 8.0 * R * K + 4.0 * K * K, 2.0 * R * K * K);
-  gemm_nn(h->stream, R, K, K, X, ldx, Ri, K, nullptr, 1.0f, 0.0f, out, ldo);
+  gemm_nn(h->stream, R, K, K, X, ldx, Ri, K, nullptr, 1.0f, 0.0f, out, ldo, skip_if);
 }
 
 // Orthonormal basis of range(X) (m x K, zero columns allowed) into out.
 // Shifted CholeskyQR followed by CholeskyQR2 (three passes).  X is clobbered.
+// For 16 < K <= 64 the third pass is decided on the device: when the second
+// pass's Gram is within 1e-2 of I (the first pass already left the block
+// orthonormal to that level) the second pass's result is final and the third
+// only copies it, with no host round trip.
 // ref_diag: optional column norms^2 of X before it was projected.
 void orth_block(mc_handle h, int64_t R, int K, float *X, int ldx, float *out, int ldo,
                 const float *ref_diag = nullptr) {
   float *tmp = fbuf(h, h->Tmp, (size_t)R * K);
+  const bool dev_skip = K > 16 && K <= 64 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
+                        h->flags.p != nullptr && h->flags.cap >= sizeof(int) * 8;
+  int *flag = dev_skip ? h->flags.as<int>() + 4 : nullptr;
   cholqr_pass(h, R, K, X, ldx, tmp, K, 1e-6f, ref_diag);
-  cholqr_pass(h, R, K, tmp, K, X, ldx, 0.0f);
-  cholqr_pass(h, R, K, X, ldx, out, ldo, 0.0f);
+  cholqr_pass(h, R, K, tmp, K, X, ldx, 0.0f, nullptr, flag);
+  cholqr_pass(h, R, K, X, ldx, out, ldo, 0.0f, nullptr, nullptr, flag);
 }
 
 // X -= Qp (Qp^T X), twice (block classical Gram-Schmidt, reorthogonalised).
@@ -1089,8 +1099,8 @@ mc_status mc_create(mc_handle *out, int64_t m, int64_t n, int64_t nnz, const int
     rp64.reserve(h->alloc, sizeof(int64_t) * (m + 1));
     copy_in(s, rp64.p, row_ptr, sizeof(int64_t) * (m + 1));
     h->rp.reserve(h->alloc, sizeof(int) * (m + 1));
-    h->flags.reserve(h->alloc, sizeof(int) * 4);
-    MC_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * 4, s));
+    h->flags.reserve(h->alloc, sizeof(int) * 8);
+    MC_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * 8, s));
     convert_rowptr(s, m, nnz, rp64.as<int64_t>(), h->rp.as<int>(), h->flags.as<int>());
     int fl[4] = {0, 0, 0, 0};
     MC_CUDA(cudaMemcpyAsync(fl, h->flags.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
@@ -1468,6 +1478,8 @@ mc_status mc_orth_block(int64_t R, int K, float *X, int ldx, const float *Qp, in
     h->stream = static_cast<cudaStream_t>(stream);
     h->alloc.stream = h->stream;
     h->m = R;
+    h->flags.reserve(h->alloc, sizeof(int) * 8);
+    MC_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * 8, h->stream));
     orth_step(h.get(), R, K, X, ldx, Qp, ldq, cols, out, ldo);
     sync(h.get());
     return MC_OK;

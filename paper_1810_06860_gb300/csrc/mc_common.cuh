@@ -176,12 +176,16 @@ void sample_lowrank(cudaStream_t st, int64_t count, const int64_t *rows, const i
 // ld_y).  sym: X == Y and only the lower triangle is needed (mirrored).
 // partial: scratch of gemm_tn_scratch_floats(R, K1, K2) floats.
 size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2);
+// skip (device int, may be NULL): when it holds a nonzero value the kernels
+// return without work (a CholeskyQR pass found unnecessary on the device).
 void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y,
-             int ld_y, float *C, int ld_c, bool sym, float *partial);
+             int ld_y, float *C, int ld_c, bool sym, float *partial, const int *skip = nullptr);
 // Z (R x K2, ld_z) = beta * Z + alpha * X (R x K1, ld_x) * W (K1 x K2, ld_w) * diag(colscale)
-// colscale may be NULL (ones).  Z may not alias X.
+// colscale may be NULL (ones).  Z may not alias X.  copy_if (device int, may
+// be NULL; 16 < K1 == K2 <= 64 only): when it holds a nonzero value, Z = X.
 void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W,
-             int ld_w, const float *colscale, float alpha, float beta, float *Z, int ld_z);
+             int ld_w, const float *colscale, float alpha, float beta, float *Z, int ld_z,
+             const int *copy_if = nullptr);
 // out (K x ncp) = W[:, 0:ncols], zero columns ncols..ncp-1
 void select_cols(cudaStream_t st, int K, const float *W, int ld_w, int ncols, int ncp, float *out);
 // In-place Cholesky of the K x K Gram G (ld) followed by inversion of the
@@ -190,8 +194,12 @@ void select_cols(cudaStream_t st, int K, const float *W, int ld_w, int ncols, in
 // shift_rel: shift = shift_rel * trace(G) / K.  ref_diag (optional, device, K
 // floats): column norms^2 before a projection; columns with G_jj <= ref_tol *
 // ref_diag[j] are treated as absent (dependent on the earlier blocks).
+// skip_if (device int, may be NULL): return without work when it is nonzero.
+// set_skip (device int, may be NULL; K <= 128): receives 1 when G is within
+// 1e-2 of the identity entry by entry (the input block was already
+// orthonormal to that level, so one more pass would change nothing), else 0.
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag,
-              float ref_tol, float *Rinv);
+              float ref_tol, float *Rinv, const int *skip_if = nullptr, int *set_skip = nullptr);
 // out[c] = sum_r X[r][c]^2 (deterministic).  scratch: colsumsq_scratch_floats(K).
 size_t colsumsq_scratch_floats(int K);
 void colsumsq(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *out, float *scratch);
