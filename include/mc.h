@@ -355,6 +355,18 @@ mc_status mc_gram(int64_t R, int K, const float *X, float *G);
  * a TMA or MMA barrier expired. */
 mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G);
 
+/* mc_panel_gemm: Z = X W of a tall X (R x K, row-major) and a small W (K x N,
+ * row-major) into Z (R x N, row-major): the panel products of the block
+ * orthonormalisation (X R^{-1} of a CholeskyQR pass, X - Q_prev C of a
+ * projection) and of the Ritz factors (U = Q W of Alg. 5 step 11, V = B^T W
+ * S^{-1} of Alg. 3 step 4).  tensor_cores = 1 runs the tcgen05 kernel (TF32
+ * operands split into hi and lo parts, float32 accumulation: about float32
+ * accuracy); it takes N <= 256 with K and N rounded up to 32 and 16 of product
+ * at most 16384, else MC_EINVAL (nothing run).  tensor_cores = 0 runs the SIMT
+ * kernels.  Host or device pointers; synchronous; MC_ETIMEOUT if a bounded
+ * wait of the tensor-core kernel expired. */
+mc_status mc_panel_gemm(int64_t R, int K, int N, const float *X, const float *W, float *Z, int tensor_cores);
+
 /* mc_gram_noalloc: G = X^T X (K x K, leading dimension ldg) of a tall device
  * matrix X (R rows, K columns, leading dimension ld, ld a multiple of 4, base
  * address 16-byte aligned), like mc_gram but without allocating any device

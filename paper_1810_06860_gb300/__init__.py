@@ -317,6 +317,19 @@ def gram(X, tensor_cores: bool = False):
     return G
 
 
+def panel_gemm(X, W, tensor_cores: bool = True):
+    """Z = X W of a tall float32 X (R x K) and a small W (K x N) (mc_panel_gemm)."""
+    lib = load()
+    X = np.ascontiguousarray(X, np.float32)
+    W = np.ascontiguousarray(W, np.float32)
+    R, K = X.shape
+    N = W.shape[1]
+    Z = np.empty((R, N), np.float32)
+    _check(lib.mc_panel_gemm(R, K, N, X.ctypes.data_as(C.c_void_p), W.ctypes.data_as(C.c_void_p),
+                             Z.ctypes.data_as(C.c_void_p), 1 if tensor_cores else 0), "mc_panel_gemm")
+    return Z
+
+
 def orth_block(X, Qp=None, stream=None):
     """Orthonormal basis of (I - Qp Qp^T) X for CUDA float32 tensors X (R x K)
     and Qp (R x cols), K and cols multiples of 4 (mc_orth_block).  X is

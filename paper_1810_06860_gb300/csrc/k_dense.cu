@@ -1177,8 +1177,30 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
   MC_CHECK_LAUNCH();
 }
 
+// The tensor-core panel product is opt-in (MC_NN_TC=1): with W's hi and lo
+// copies resident in shared memory too few X boxes stay in flight per SM, and
+// it measured no faster than the SIMT kernels (equal at K = 60, slower at
+// K = 180 and 240).
+bool use_nn_tc() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_NN_TC");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
 void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W, int ld_w,
-             const float *colscale, float alpha, float beta, float *Z, int ld_z, const int *copy_if) {
+             const float *colscale, float alpha, float beta, float *Z, int ld_z, const int *copy_if, int *err) {
+  if (R <= 0 || K2 <= 0) return;
+  if (use_nn_tc() && K2 > 16 && gemm_nn_tc_supported(R, K1, K2, X, ld_x) && (!copy_if || K1 == K2)) {
+    gemm_nn_tc(st, R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, Z, ld_z, err, copy_if);
+    return;
+  }
+  gemm_nn_simt(st, R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, Z, ld_z, copy_if);
+}
+
+void gemm_nn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W, int ld_w,
+                  const float *colscale, float alpha, float beta, float *Z, int ld_z, const int *copy_if) {
   if (R <= 0 || K2 <= 0) return;
   MC_REQUIRE(!copy_if || (K1 == K2 && K2 > 16 && K1 <= 64 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0),
              "gemm_nn: the copy mode needs the small-factor kernel (16 < K1 == K2 <= 64, X 16-byte aligned)");

@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 namespace mc {
@@ -316,6 +318,233 @@ gram_tc_reduce_kernel(int K, int nsplit, const float *__restrict__ partial, int 
   }
 }
 
+// ---- panel times small factor on the tensor cores ---------------------------
+// Z (R x N) = alpha X (R x K) W (K x N) diag(colscale) + beta Z, float32 in and
+// out, for K_p N_p <= 16384 (K_p = K rounded up to 32, N_p = N rounded up to
+// 32): the block products of the Krylov orthonormalisation (X R^{-1},
+// X - Q_prev C) and the Ritz factors U = Q W, V = B^T W S^{-1} (Alg. 5 step
+// 11, Alg. 3 step 4).
+//
+// One CTA of 128 threads per SM walks 128-row tiles of X.  TMA brings each
+// tile in 32-column boxes (128-byte rows, 128-byte swizzle), which is already
+// the K-major operand layout of tcgen05.mma; the threads split each box in
+// place into a TF32 "hi" part and a float32 remainder "lo".  W, staged once per
+// CTA, is written transposed into the same layout (hi and lo).  One thread
+// issues hi*hi + hi*lo + lo*hi per 8-column k-step into a 128 x N_p float32
+// accumulator in tensor memory (about float32 accuracy); a box's stage is
+// reloaded once the MMAs reading it have completed.  After the last box of a
+// tile each warp reads its 32 accumulator rows (tcgen05.ld) and writes the
+// epilogue.  Every mbarrier wait is bounded; on expiry the kernel records an
+// error code, waits (bounded) for its outstanding copies and MMAs, frees its
+// tensor memory and returns.
+constexpr int NT_THREADS = 128, NT_BM = 128, NT_KC = 32;
+constexpr int NT_BOX_BYTES = NT_BM * NT_KC * 4;  // 16 KiB
+constexpr int NT_MAX_W = 16384;                   // K_p * N_p floats
+constexpr size_t NT_SMEM_LIMIT = 220 * 1024;
+
+__global__ void __launch_bounds__(NT_THREADS, 2)
+gemm_nn_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int N, int Kp, int Np,
+                  uint32_t tmem_cols, int nst, const float *__restrict__ W, int ld_w,
+                  const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z, int ld_z,
+                  int *__restrict__ err, const int *__restrict__ copy_if, int ld_x, const float *__restrict__ Xp) {
+  extern __shared__ __align__(1024) uint8_t nt_raw_smem[];
+  if (copy_if && *copy_if) {
+    // copy mode (the factor is the identity: a pass the previous one made
+    // unnecessary): Z = X, K == N
+    for (int64_t e = blockIdx.x * (int64_t)NT_THREADS + threadIdx.x; e < R * K; e += (int64_t)gridDim.x * NT_THREADS) {
+      const int64_t r = e / K;
+      const int c = static_cast<int>(e % K);
+      Z[r * ld_z + c] = Xp[r * ld_x + c];
+    }
+    return;
+  }
+  __shared__ __align__(8) uint64_t full_bar[4];
+  __shared__ __align__(8) uint64_t mma_bar[4];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int s_fail;  // failure codes, for the report only (control uses barrier votes)
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(nt_raw_smem) + 1023) & ~uintptr_t(1023));
+  const int kchunks = Kp / NT_KC;
+  const size_t wbytes = (size_t)Kp * Np * 4;  // one of hi / lo
+  uint8_t *whi = base, *wlo = base + wbytes;
+  uint8_t *stg = base + 2 * wbytes;           // nst stages of (hi, lo) boxes
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (R + NT_BM - 1) / NT_BM;
+  const int my_tiles = blockIdx.x < ntiles ? static_cast<int>((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int G = my_tiles * kchunks;           // boxes this CTA consumes
+
+  if (tid == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&mma_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // W^T (N_p x K_p, K-major, 128-byte swizzle) as hi and lo: element (n, k) of
+  // column block kc at kc * N_p * 128 + (n / 8) * 1024 + (n % 8) * 128 +
+  // (((k % 32) / 4) ^ (n % 8)) * 16 + (k % 4) * 4
+  for (int k = wid; k < Kp; k += NT_THREADS / 32) {  // a warp per row of W, lanes along it
+    const int kc = k / NT_KC, kl = k % NT_KC;
+    for (int n = lane; n < Np; n += 32) {
+      const float w = (k < K && n < N) ? W[(int64_t)k * ld_w + n] : 0.f;
+      const float h = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
+      const size_t off =
+          (size_t)kc * Np * 128 + (n >> 3) * 1024 + (n & 7) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
+      *reinterpret_cast<float *>(whi + off) = h;
+      *reinterpret_cast<float *>(wlo + off) = w - h;
+    }
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  auto box_hi = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES; };
+  auto box_lo = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES + NT_BOX_BYTES; };
+  auto issue = [&](int g) {
+    const int s = g % nst;
+    const int tl = g / kchunks, kc = g % kchunks;
+    const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
+    mbar_expect_tx(&full_bar[s], NT_BOX_BYTES);
+    tma_load_2d(box_hi(s), &xmap, kc * NT_KC, static_cast<int>(tile * NT_BM), &full_bar[s]);
+  };
+  // only tid 0 issues copies and MMAs, so it alone tracks how far both got
+  int issued = 0, committed = -1;
+  if (tid == 0)
+    for (; issued < G && issued < nst; ++issued) issue(issued);
+  const uint32_t idesc = idesc_tf32(NT_BM, Np);
+  const bool vec_out = ld_z % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15u) == 0;
+  const uint32_t wstride = static_cast<uint32_t>(Np) * 128;
+  int lf = 0;  // this thread saw a wait expire
+  for (int g = 0; g < G; ++g) {
+    const int s = g % nst, kc = g % kchunks, tl = g / kchunks;
+    if (!mbar_wait(&full_bar[s], (g / nst) & 1)) {
+      lf = 1;
+      atomicOr(&s_fail, 1);
+    }
+    // split the box in place: hi stays, lo goes to the stage's second box
+    float4 *hi4 = reinterpret_cast<float4 *>(box_hi(s));
+    float4 *lo4 = reinterpret_cast<float4 *>(box_lo(s));
+    for (int q = tid; q < NT_BOX_BYTES / 16; q += NT_THREADS) {
+      const float4 v = hi4[q];
+      float4 h, l;
+      h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+      h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+      h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+      h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+      l.x = v.x - h.x;
+      l.y = v.y - h.y;
+      l.z = v.z - h.z;
+      l.w = v.w - h.w;
+      hi4[q] = h;
+      lo4[q] = l;
+    }
+    fence_proxy_async();
+    if (__syncthreads_or(lf)) break;  // a block-wide vote: every thread leaves together
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ah = smem_u32(box_hi(s)), al = smem_u32(box_lo(s));
+      const uint32_t bh = smem_u32(whi) + kc * wstride, bl = smem_u32(wlo) + kc * wstride;
+#pragma unroll
+      for (int ks = 0; ks < NT_KC / 8; ++ks) {
+        const uint32_t ko = ks * 32;
+        const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, acc0);
+        mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
+        mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
+      }
+      mma_commit(&mma_bar[s]);
+      committed = g;
+      if (kc == kchunks - 1) mma_commit(&acc_bar);
+      // refill the stage of the previous box once its MMAs have read it
+      if (g >= 1 && issued < G) {
+        const int gp = g - 1;
+        if (mbar_wait(&mma_bar[gp % nst], (gp / nst) & 1)) {
+          issue(issued);
+          ++issued;
+        } else {
+          lf = 1;
+          atomicOr(&s_fail, 2);
+        }
+      }
+    }
+    if (kc == kchunks - 1) {
+      // epilogue of the tile: wait for its MMAs, then each warp its 32 rows
+      if (!mbar_wait(&acc_bar, tl & 1)) {
+        lf = 1;
+        atomicOr(&s_fail, 4);
+      }
+      const bool ok = !__syncthreads_or(lf);  // block-uniform
+      tc_fence_after();
+      // 64 columns at a time: each thread moves its accumulator row into the
+      // stage of the box just consumed (free once the MMAs are done; its
+      // refill is issued in the next iteration), float4 chunk q of row r at
+      // q ^ (r % 16); then the block writes whole rows with float4 stores
+      float4 *tile_out = reinterpret_cast<float4 *>(box_hi(s));  // 128 rows x 16 float4
+      const int64_t row0 = ((int64_t)blockIdx.x + (int64_t)tl * gridDim.x) * NT_BM;
+      const int r = 32 * wid + lane;
+      for (int c0 = 0; ok && c0 < N; c0 += 64) {
+        for (int c = 0; c < 64 && c0 + c < N; c += 16) {
+          float v[16];
+          tmem_ld16(tmem + (static_cast<uint32_t>(32 * wid) << 16) + c0 + c, v);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            tile_out[r * 16 + (((c >> 2) + u) ^ (r & 15))] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        }
+        __syncthreads();
+        const int ncol = min(64, N - c0);
+        for (int e = tid; e < NT_BM * 16; e += NT_THREADS) {
+          const int rr = e >> 4, q = e & 15, col = 4 * q;
+          const int64_t grow = row0 + rr;
+          if (grow >= R || col >= ncol) continue;
+          const float4 v4 = tile_out[rr * 16 + (q ^ (rr & 15))];
+          const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+          float *z = Z + grow * ld_z + c0 + col;
+          if (vec_out && col + 3 < ncol) {
+            float o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) o[i] = vv[i] * alpha * (colscale ? colscale[c0 + col + i] : 1.0f);
+            if (beta != 0.f) {
+              const float4 zo = *reinterpret_cast<const float4 *>(z);
+              o[0] += beta * zo.x;
+              o[1] += beta * zo.y;
+              o[2] += beta * zo.z;
+              o[3] += beta * zo.w;
+            }
+            *reinterpret_cast<float4 *>(z) = make_float4(o[0], o[1], o[2], o[3]);
+          } else {
+            for (int i = 0; i < 4 && col + i < ncol; ++i)
+              z[i] = (beta != 0.f ? beta * z[i] : 0.f) + vv[i] * alpha * (colscale ? colscale[c0 + col + i] : 1.0f);
+          }
+        }
+        __syncthreads();
+      }
+      tc_fence_before();
+      __syncthreads();  // the accumulator is read before the next tile's first MMA
+      if (!ok) break;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // after an early exit: wait for the last committed MMAs and for the
+    // copies that no MMA consumed (bounded waits; a completed phase returns at once)
+    if (committed >= 0 && !mbar_wait(&mma_bar[committed % nst], (committed / nst) & 1)) atomicOr(&s_fail, 8);
+    for (int t = committed + 1; t < issued; ++t) mbar_wait(&full_bar[t % nst], (t / nst) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  if (tid == 0 && s_fail && err) atomicOr(err, s_fail << 4);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::mutex mu;
@@ -336,6 +565,79 @@ int tc_nsplit(int64_t R) {
 }
 
 }  // namespace
+
+// ---- panel x small factor (tensor cores) --------------------------------------
+namespace {
+struct NtPlan {
+  int Kp, Np, nst, ctas;
+  uint32_t cols;
+  size_t smem;
+};
+// CTAs per SM: two when W and two stages fit in half the shared memory
+// (MC_NT_CTAS=1 keeps one CTA with up to four stages).
+int nt_ctas_pref() {
+  static const int v = [] {
+    const char *e = std::getenv("MC_NT_CTAS");
+    return (e && e[0] == '1') ? 1 : 2;
+  }();
+  return v;
+}
+
+NtPlan nt_plan(int K, int N) {
+  NtPlan p{};
+  p.Kp = static_cast<int>(round_up(K, NT_KC));
+  p.Np = static_cast<int>(round_up(N, 16));
+  const size_t wbytes = (size_t)p.Kp * p.Np * 4;
+  const size_t half = 110 * 1024;
+  p.ctas = 1;
+  size_t limit = NT_SMEM_LIMIT;
+  if (nt_ctas_pref() == 2 && 2 * wbytes + 2 * 2 * NT_BOX_BYTES + 1024 <= half) {
+    p.ctas = 2;
+    limit = half;
+  }
+  const size_t avail = limit > 2 * wbytes + 1024 ? limit - 2 * wbytes - 1024 : 0;
+  p.nst = static_cast<int>(std::min<size_t>(4, avail / (2 * NT_BOX_BYTES)));
+  p.smem = 2 * wbytes + (size_t)p.nst * 2 * NT_BOX_BYTES + 1024;
+  p.cols = 32;
+  while (p.cols < static_cast<uint32_t>(p.Np)) p.cols <<= 1;
+  return p;
+}
+}  // namespace
+
+bool gemm_nn_tc_supported(int64_t R, int K, int N, const void *X, int ld_x) {
+  if (R < 1 || R >= (int64_t(1) << 31) || K < 1 || N < 1 || N > 256 || ld_x < K || ld_x % 4 != 0) return false;
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return false;
+  const NtPlan p = nt_plan(K, N);
+  return (int64_t)p.Kp * p.Np <= NT_MAX_W && p.nst >= 2;
+}
+
+void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld_x, const float *W, int ld_w,
+                const float *colscale, float alpha, float beta, float *Z, int ld_z, int *err, const int *copy_if) {
+  MC_REQUIRE(gemm_nn_tc_supported(R, K, N, X, ld_x), "gemm_nn_tc: shape or alignment not supported");
+  MC_REQUIRE(!copy_if || K == N, "gemm_nn_tc: the copy mode needs K == N");
+  const NtPlan p = nt_plan(K, N);
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(R)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld_x) * sizeof(float)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(NT_KC), static_cast<cuuint32_t>(NT_BM)};
+  const cuuint32_t estride[2] = {1, 1};
+  const CUresult cr = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), gdim, gstride, box,
+                                  estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) fail(MC_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)cr));
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    MC_CUDA(cudaGetDevice(&dev));
+    MC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t ntiles = (R + NT_BM - 1) / NT_BM;
+  const int grid = static_cast<int>(std::min<int64_t>(ntiles, (int64_t)sms * p.ctas));
+  MC_CUDA(cudaFuncSetAttribute(gemm_nn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NT_SMEM_LIMIT));
+  gemm_nn_tc_kernel<<<grid, NT_THREADS, p.smem, st>>>(map, R, K, N, p.Kp, p.Np, p.cols, p.nst, W, ld_w, colscale,
+                                                       alpha, beta, Z, ld_z, err, copy_if, ld_x, X);
+  MC_CHECK_LAUNCH();
+}
 
 size_t gram_tc_scratch_floats(int64_t R, int K) {
   const int Kp = static_cast<int>(round_up(K, 32));

@@ -451,6 +451,10 @@ void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_ou
   run(cfg);
 }
 
+// Device flag of the handle that the tensor-core kernels raise when a bounded
+// wait expires (checked after every Ritz eigensolve).
+int *tc_err(mc_handle h) { return h->flags.p ? h->flags.as<int>() + 3 : nullptr; }
+
 // Gram X^T X: the tensor-core kernel (tcgen05, 3xTF32) for tc_min_k() <= K
 // <= 256, SIMT otherwise; MC_GRAM_SIMT=1 selects SIMT everywhere.
 bool use_tensor_gram() {
@@ -495,7 +499,7 @@ void cholqr_pass(mc_handle h, int64_t R, int K, const float *X, int ldx, float *
     chol_inv(h->stream, K, G, K, shift_rel, ref_diag, 1e-10f, Ri, skip_if, set_skip);
   }
   Scope sc(h, MC_T_GEMM, 8.0 * R * K + 4.0 * K * K, 2.0 * R * K * K);
-  gemm_nn(h->stream, R, K, K, X, ldx, Ri, K, nullptr, 1.0f, 0.0f, out, ldo, skip_if);
+  gemm_nn(h->stream, R, K, K, X, ldx, Ri, K, nullptr, 1.0f, 0.0f, out, ldo, skip_if, tc_err(h));
 }
 
 // Orthonormal basis of range(X) (m x K, zero columns allowed) into out.
@@ -527,7 +531,7 @@ void project_out(mc_handle h, int64_t R, const float *Qp, int ldq, int cols, flo
       gemm_tn(h->stream, R, cols, K, Qp, ldq, X, ldx, C, K, false, h->tn_part.as<float>());
     }
     Scope sc(h, MC_T_GEMM, 4.0 * R * (cols + 2 * K), 2.0 * R * cols * K);
-    gemm_nn(h->stream, R, cols, K, Qp, ldq, C, K, nullptr, -1.0f, 1.0f, X, ldx);
+    gemm_nn(h->stream, R, cols, K, Qp, ldq, C, K, nullptr, -1.0f, 1.0f, X, ldx, nullptr, tc_err(h));
   }
 }
 
@@ -715,11 +719,12 @@ void form_factors(mc_handle h, const float *Qb, int ldq, int ncols, const std::v
   stage_copy(h, dsc, sc.data(), sc.size());
   if (U) {
     Scope sc(h, MC_T_GEMM, 4.0 * h->m * (Kq + ldp), 2.0 * h->m * Kq * ldp);
-    gemm_nn(h->stream, h->m, Kq, ldp, Qb, ldq, Ws, ldp, dsc, 1.0f, 0.0f, U, ldp);
+    gemm_nn(h->stream, h->m, Kq, ldp, Qb, ldq, Ws, ldp, dsc, 1.0f, 0.0f, U, ldp, nullptr, tc_err(h));
   }
   if (V) {
     Scope sc(h, MC_T_GEMM, 4.0 * h->n * (Kq + ldp), 2.0 * h->n * Kq * ldp);
-    gemm_nn(h->stream, h->n, Kq, ldp, h->Bt.as<float>(), Kq, Ws, ldp, dsc + ldp, 1.0f, 0.0f, V, ldp);
+    gemm_nn(h->stream, h->n, Kq, ldp, h->Bt.as<float>(), Kq, Ws, ldp, dsc + ldp, 1.0f, 0.0f, V, ldp, nullptr,
+            tc_err(h));
   }
 }
 
@@ -931,7 +936,8 @@ mc_status svt_step(mc_handle h, mc_iter_info *out) {
       std::vector<float> eye((size_t)h->ub_ld * ldp, 0.f);
       for (int j = 0; j < r; ++j) eye[(size_t)j * ldp + j] = (float)su[j];
       stage_copy(h, Ws, eye.data(), eye.size());
-      gemm_nn(h->stream, h->m, h->ub_ld, ldp, h->Ub.as<float>(), h->ub_ld, Ws, ldp, nullptr, 1.0f, 0.0f, Us, ldp);
+      gemm_nn(h->stream, h->m, h->ub_ld, ldp, h->Ub.as<float>(), h->ub_ld, Ws, ldp, nullptr, 1.0f, 0.0f, Us, ldp,
+              nullptr, tc_err(h));
     } else {
       form_factors(h, Qb, ldq, r, su, sv, Us, Vr, ldp);
     }
@@ -1460,6 +1466,36 @@ mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G) {
     cudaFree(part);
     cudaFree(derr);
     if (herr) fail(MC_ETIMEOUT, "a bounded wait in the tensor-core Gram expired");
+    return MC_OK;
+  });
+}
+
+mc_status mc_panel_gemm(int64_t R, int K, int N, const float *X, const float *W, float *Z, int tensor_cores) {
+  if (R < 1 || K < 1 || N < 1 || !X || !W || !Z) return MC_EINVAL;
+  const int kp = (int)round_up(K, 4);
+  if (tensor_cores && !gemm_nn_tc_supported(R, K, N, reinterpret_cast<const void *>(256), kp)) return MC_EINVAL;
+  return guarded([&]() -> mc_status {
+    DBuf dX, dW, dZ, de;
+    Alloc a;
+    BufGuard g(a, {&dX, &dW, &dZ, &de});
+    dX.reserve(a, sizeof(float) * R * kp);
+    dW.reserve(a, sizeof(float) * K * N);
+    dZ.reserve(a, sizeof(float) * R * N);
+    de.reserve(a, sizeof(int));
+    MC_CUDA(cudaMemset(de.p, 0, sizeof(int)));
+    MC_CUDA(cudaMemset(dX.p, 0, sizeof(float) * R * kp));
+    MC_CUDA(cudaMemcpy2D(dX.p, sizeof(float) * kp, X, sizeof(float) * K, sizeof(float) * K, R, cudaMemcpyDefault));
+    MC_CUDA(cudaMemcpy(dW.p, W, sizeof(float) * K * N, cudaMemcpyDefault));
+    if (tensor_cores)
+      gemm_nn_tc(0, R, K, N, dX.as<float>(), kp, dW.as<float>(), N, nullptr, 1.0f, 0.0f, dZ.as<float>(), N,
+                 de.as<int>());
+    else
+      gemm_nn_simt(0, R, K, N, dX.as<float>(), kp, dW.as<float>(), N, nullptr, 1.0f, 0.0f, dZ.as<float>(), N);
+    int herr = 0;
+    MC_CUDA(cudaMemcpy(&herr, de.p, sizeof(int), cudaMemcpyDeviceToHost));
+    MC_CUDA(cudaMemcpy(Z, dZ.p, sizeof(float) * R * N, cudaMemcpyDefault));
+    MC_CUDA(cudaDeviceSynchronize());
+    if (herr) fail(MC_ETIMEOUT, "a bounded wait in the tensor-core panel product expired");
     return MC_OK;
   });
 }

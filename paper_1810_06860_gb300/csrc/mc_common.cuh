@@ -183,9 +183,16 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
 // Z (R x K2, ld_z) = beta * Z + alpha * X (R x K1, ld_x) * W (K1 x K2, ld_w) * diag(colscale)
 // colscale may be NULL (ones).  Z may not alias X.  copy_if (device int, may
 // be NULL; 16 < K1 == K2 <= 64 only): when it holds a nonzero value, Z = X.
+// With MC_NN_TC=1 the shapes the tensor-core kernel takes (K2 > 16) run there;
+// err (device int, may be NULL) receives its wait-expiry code.
 void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W,
              int ld_w, const float *colscale, float alpha, float beta, float *Z, int ld_z,
-             const int *copy_if = nullptr);
+             const int *copy_if = nullptr, int *err = nullptr);
+// The SIMT kernels alone (thread-per-row for K2 <= 16, W in shared memory for
+// K1 <= 64, tiled otherwise).
+void gemm_nn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W,
+                  int ld_w, const float *colscale, float alpha, float beta, float *Z, int ld_z,
+                  const int *copy_if = nullptr);
 // out (K x ncp) = W[:, 0:ncols], zero columns ncols..ncp-1
 void select_cols(cudaStream_t st, int K, const float *W, int ld_w, int ncols, int ncp, float *out);
 // In-place Cholesky of the K x K Gram G (ld) followed by inversion of the
@@ -221,6 +228,14 @@ bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const flo
 size_t gram_tc_scratch_floats(int64_t R, int K);
 bool gram_tc_supported(int K, int ld, const void *X);
 void gram_tc(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *G, int ld_g, float *partial, int *err);
+// Z (R x N, ld_z) = beta Z + alpha X (R x K, ld_x) W (K x N, ld_w) diag(colscale)
+// on the tensor cores (k_tc.cu, 3xTF32).  Supported: N <= 256, K and N
+// rounded up to 32 and 16 with a product of at most 16384, ld_x % 4 == 0, X
+// 16-byte aligned.  err as for gram_tc (codes shifted by 4 bits).
+bool gemm_nn_tc_supported(int64_t R, int K, int N, const void *X, int ld_x);
+void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld_x, const float *W, int ld_w,
+                const float *colscale, float alpha, float beta, float *Z, int ld_z, int *err,
+                const int *copy_if = nullptr);
 // Top-kw eigenpairs of the symmetric K x K matrix A (lower triangle read).
 // lam: kw floats descending; W: K x kw (ld_w).  work: eig_work_bytes(K, kw).
 size_t eig_work_bytes(int K, int kw);

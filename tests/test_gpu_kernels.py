@@ -237,3 +237,29 @@ def test_coo_ingest_matches_csr(mc):
         mc.Handle.from_coo(4, 4, np.array([0, 4], np.int64), np.array([2, 3], np.int32), np.ones(2, np.float32))
     empty = mc.Handle.from_coo(5, 3, np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
     empty.close()
+
+
+@pytest.mark.parametrize("R,K,N", [(138_000, 60, 60), (27_000, 240, 52), (50_001, 180, 60), (300, 7, 13),
+                                   (129, 32, 16), (5_000, 256, 64), (1_000, 64, 256)])
+def test_panel_gemm_tensor_cores(mc, R, K, N):
+    """Z = X W on the tensor cores (3xTF32) against a float64 product: every
+    entry within 1e-5 of max |X| |W| (the bound of a float32 sum over K terms
+    with the TF32 split's error of about 2^-22 per product), and against the
+    SIMT kernels.  Ragged R (not a multiple of the 128-row tile), K and N (not
+    multiples of the 32-column box or 16-column MMA) are covered."""
+    rng = np.random.default_rng(R + K + N)
+    X = rng.standard_normal((R, K)).astype(np.float32)
+    W = (rng.standard_normal((K, N)) / np.sqrt(K)).astype(np.float32)
+    Z = mc.panel_gemm(X, W, tensor_cores=True)
+    ref = X.astype(np.float64) @ W.astype(np.float64)
+    bound = np.abs(X).astype(np.float64) @ np.abs(W).astype(np.float64)
+    assert np.all(np.abs(Z - ref) <= 1e-5 * bound.max())
+    Zs = mc.panel_gemm(X, W, tensor_cores=False)
+    assert np.max(np.abs(Z - Zs)) <= 2e-5 * bound.max()
+
+
+def test_panel_gemm_tensor_cores_rejects_wide(mc):
+    X = np.zeros((10, 256), np.float32)
+    W = np.zeros((256, 128), np.float32)  # 256 x 128 > 16384
+    with pytest.raises(mc.McError):
+        mc.panel_gemm(X, W, tensor_cores=True)
