@@ -107,10 +107,11 @@ class SvtResult:
 
 def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, p0=3, p_min=3,
              p_max=20, i_max=1000, i_reuse=50, q_reuse=10, recycle=1, seed=0, callback=None,
-             on_factors=None) -> SvtResult:
+             on_factors=None, on_update=None) -> SvtResult:
     """Alg. 6.  ``recycle``: 0 none, 1 reuse Q, 2 reuse U, 3 warm-started Omega.
     ``callback(rec)`` receives each iteration's record; ``on_factors(rec, Us,
-    V)`` also the factors of X^i (for metrics that need the estimate)."""
+    V)`` also the factors of X^i (for metrics that need the estimate);
+    ``on_update(rec, y)`` the values of Y^i on Phi (CSR order) after step 16."""
     A = as_csr64(m, n, row_ptr, col, val)
     M = A.data.copy()
     rows = np.repeat(np.arange(m), np.diff(np.asarray(row_ptr)))
@@ -193,6 +194,8 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
         if err < eps:
             return SvtResult(Us, Vr, sig, it, err, True, history)
         Y.data = Y.data + delta * (M - x)
+        if on_update is not None:
+            on_update(rec, Y.data)
         p, streak = adapt_p(p, streak, err, prev_err, p_min, p_max)
         prev_err = err
     return SvtResult(Us, Vr, sig, it, err, False, history)

@@ -139,6 +139,45 @@ def test_svt_config1_matches_oracle(mc):
     assert np.linalg.norm(X - o.dense) / np.linalg.norm(o.dense) < 1e-3
 
 
+@pytest.mark.parametrize("case", ["config1", "zipf"])
+def test_svt_iterate_matches_oracle_elementwise(mc, case):
+    """Y^i on Phi (Alg. 6 step 16) entry by entry against the oracle's after
+    1, 5 and 20 iterations.  Bound: each step adds delta (M - x^i) on Phi, and
+    the per-iteration parity of the estimate on Phi is 1e-4 of the data
+    (the error tolerance of the trajectory tests), so after i steps an entry
+    may differ by delta * i * 1e-4 * max|M| and the whole vector by
+    delta * i * 1e-4 * ||P_Phi M||_F.  A wrong sign, a dropped term or a
+    misplaced entry in the fused update exceeds that at the first step."""
+    if case == "config1":
+        o = mc_synth.lowrank_uniform(500, 500, 10, frac=0.2, seed=0)
+        kw = dict(tau=2500.0, delta=6.0, eps=1e-4, recycle=3, seed=0)
+    else:
+        o = mc_synth.ratings(m=4000, n=1200, N=150_000, seed=2)
+        kw = dict(tau=5.0 * 1200, delta=1.9, eps=1e-4, recycle=3, seed=4)
+    checks = (1, 5, 20)
+    ys = {}
+
+    def keep(rec, y):
+        if rec["i"] in checks:
+            ys[rec["i"]] = y.copy()
+
+    osvt.svt_fast(o.m, o.n, o.row_ptr, o.col, o.val, i_max=max(checks), on_update=keep, **kw)
+    m_max = float(np.max(np.abs(o.val)))
+    m_fro = float(np.linalg.norm(o.val.astype(np.float64)))
+    prm = mc.params(**kw, i_max=1000)
+    with mc.Handle.from_observed(o) as h:
+        for i in range(1, max(checks) + 1):
+            info = h.svt_step(prm)
+            assert not info["converged"]
+            if i in checks:
+                got = h.get_values().astype(np.float64)
+                want = ys[i]
+                assert got.shape == want.shape
+                d = np.abs(got - want)
+                assert np.max(d) <= kw["delta"] * i * 1e-4 * m_max, (i, float(np.max(d)))
+                assert np.linalg.norm(got - want) <= kw["delta"] * i * 1e-4 * m_fro, i
+
+
 def test_svt_recycle_q_matches_oracle(mc):
     o = mc_synth.lowrank_uniform(500, 500, 10, frac=0.2, seed=0)
     ref, hist, _ = _svt_compare(mc, o, dict(tau=2500.0, delta=6.0, eps=1e-4, recycle=1, i_reuse=50, q_reuse=2,

@@ -210,3 +210,23 @@ def test_svt_fast_follows_p_rule(c1_recycle_q):
         p, prev = p2, a["err"]
         assert b["p"] == p
     assert ups >= 1 and downs >= 1
+
+
+def test_stored_image_solve_reproduces():
+    """The stored image-inpainting solve (tests/golden/image_svt_oracle.json)
+    is the current oracle's: its first iterations replay exactly."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "image_svt_oracle.json")) as f:
+        ref = json.load(f)
+    w = ref["workload"]
+    o = mc_synth.smooth_image(w["size"], w["size"], w["rank"], sigma_px=w["sigma_px"], frac=w["frac"],
+                              seed=w["seed"])
+    kw = dict(ref["params"])
+    kw["i_max"] = 4
+    res = svt.svt_fast(o.m, o.n, o.row_ptr, o.col, o.val, **kw)
+    for a, b in zip(res.history, ref["history"][:4]):
+        assert (a["k"], a["r"], a["p"]) == (b["k"], b["r"], b["p"])
+        assert a["err"] == pytest.approx(b["err"], rel=1e-12)
+    assert ref["converged"] and ref["rank"] == 41 and ref["recovery_rel_err"] < 1e-3
