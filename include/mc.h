@@ -74,6 +74,7 @@ typedef struct {
   int recycle;    /* 0 none, 1 reuse Q, 2 reuse U (Sec. IV.B), 3 warm-start Omega with V */
   int k_max;      /* cap on the SVD rank (0 = min(m,n) - s) */
   int precision;  /* 0 plain float32, 1 bf16 panels in the Krylov products */
+  int inner;      /* SVD of each fresh call: 0 rSVD-BKI (Alg. 5, Alg. 6 step 6), 1 rSVD-PI (Alg. 4) */
   uint64_t seed;  /* key of the Philox stream that draws Omega */
 } mc_params;
 

@@ -43,7 +43,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .philox import omega
-from .rsvd import as_csr64, clamp_rank, recycle_q, recycle_u, rsvd_bki
+from .rsvd import as_csr64, clamp_rank, recycle_q, recycle_u, rsvd_bki, rsvd_pi
 
 
 def default_tau(m: int, n: int) -> float:
@@ -107,8 +107,10 @@ class SvtResult:
 
 def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, p0=3, p_min=3,
              p_max=20, i_max=1000, i_reuse=50, q_reuse=10, recycle=1, seed=0, callback=None,
-             on_factors=None, on_update=None) -> SvtResult:
+             on_factors=None, on_update=None, inner=0) -> SvtResult:
     """Alg. 6.  ``recycle``: 0 none, 1 reuse Q, 2 reuse U, 3 warm-started Omega.
+    ``inner``: the SVD of a fresh call, 0 rSVD-BKI (Alg. 5, as Alg. 6 states)
+    or 1 rSVD-PI (Alg. 4, one block of k + s columns whatever p).
     ``callback(rec)`` receives each iteration's record; ``on_factors(rec, Us,
     V)`` also the factors of X^i (for metrics that need the estimate);
     ``on_update(rec, y)`` the values of Y^i on Phi (CSR order) after step 16."""
@@ -144,7 +146,11 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
         used_recycle = False
         margin = math.inf  # closest any computed sigma came to tau, relative (a conditioning record only)
         while True:
-            kk, pp = clamp_rank(m, n, k, s, p)
+            if inner == 1:
+                kk, _ = clamp_rank(m, n, k, s, 0)
+                pp = p
+            else:
+                kk, pp = clamp_rank(m, n, k, s, p)
             width_ok = basis is not None and (recycle != 2 or basis.shape[1] >= kk) and \
                 (recycle != 1 or basis.shape[1] >= kk)
             fresh = (recycle in (0, 3) or it < i_reuse or q == q_reuse or not width_ok or force_fresh)
@@ -153,7 +159,7 @@ def svt_fast(m, n, row_ptr, col, val, tau=None, delta=1.2, eps=1e-4, l=5, s=10, 
                 if recycle == 3 and Vprev is not None and r > 0:
                     w = min(r, kk + s, Vprev.shape[1])
                     Om[:, :w] = Vprev[:, :w]
-                U, S, V, Q = rsvd_bki(Y, kk, pp, s, Om=Om)
+                U, S, V, Q = (rsvd_pi if inner == 1 else rsvd_bki)(Y, kk, pp, s, Om=Om)
                 call_id += 1
                 q = 0
                 basis = Q if recycle == 1 else U

@@ -14,7 +14,7 @@ class McParams(C.Structure):
     _fields_ = [("tau", C.c_double), ("delta", C.c_double), ("eps", C.c_double), ("l", C.c_int), ("s", C.c_int),
                 ("p0", C.c_int), ("p_min", C.c_int), ("p_max", C.c_int), ("i_max", C.c_int), ("i_reuse", C.c_int),
                 ("q_reuse", C.c_int), ("recycle", C.c_int), ("k_max", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64)]
+                ("inner", C.c_int), ("seed", C.c_uint64)]
 
 
 class McIterInfo(C.Structure):

@@ -613,10 +613,11 @@ void krylov_bki(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, con
 }
 
 // Power-iteration basis of Alg. 4 (steps 1-7) into h->Q (m x kbp).
-void power_pi(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id) {
+void power_pi(mc_handle h, int kb, int p, uint64_t seed, uint64_t call_id, const float *warm = nullptr,
+              int warm_ld = 0, int warm_cols = 0) {
   const bool mixed = h->precision != 0;
   const int kbp = (int)round_up(kb, block_align(h));
-  draw_omega(h, kb, kbp, seed, call_id, nullptr, 0, 0);
+  draw_omega(h, kb, kbp, seed, call_id, warm, warm_ld, warm_cols);
   float *Q = fbuf(h, h->Q, (size_t)h->m * kbp);
   float *H = fbuf(h, h->H, (size_t)h->m * kbp);
   float *T = fbuf(h, h->T, (size_t)h->n * kbp);
@@ -808,6 +809,7 @@ void svt_initialise(mc_handle h, const mc_params *prm) {
   MC_REQUIRE(P.delta > 0 && P.eps > 0 && P.l >= 1 && P.s >= 0 && P.i_max >= 1, "invalid SVT parameters");
   MC_REQUIRE(P.recycle >= 0 && P.recycle <= 3, "recycle must be 0..3");
   MC_REQUIRE(P.precision == 0 || P.precision == 1, "precision must be 0 (float32) or 1 (bf16 panels)");
+  MC_REQUIRE(P.inner == 0 || P.inner == 1, "inner must be 0 (rSVD-BKI) or 1 (rSVD-PI)");
   h->precision = P.precision;
   h->tau = P.tau > 0 ? P.tau : 5.0 * std::sqrt((double)h->m * (double)h->n);
   // Y currently holds P_Phi(M) only if no rSVD/SVT changed it; start from M.
@@ -845,9 +847,10 @@ void svt_svd(mc_handle h, int kk, int pp, bool fresh, std::vector<double> &sig, 
       warm = h->Vb.as<float>();
       wcols = std::min(std::min(h->r, kk + P.s), h->vb_k);
     }
-    krylov_bki(h, kk + P.s, pp, P.seed, h->call_id, warm, h->vb_ld, wcols);
+    if (P.inner == 1) power_pi(h, kk + P.s, pp, P.seed, h->call_id, warm, h->vb_ld, wcols);
+    else krylov_bki(h, kk + P.s, pp, P.seed, h->call_id, warm, h->vb_ld, wcols);
     h->call_id += 1;
-    ritz(h, h->Q.as<float>(), h->Kq, h->Kq, kk, true);
+    ritz(h, h->Q.as<float>(), h->Kq, h->Kq, kk, P.inner != 1);
     *Qb = h->Q.as<float>();
     *ldq = h->Kq;
     if (P.recycle == 1) h->basis = 1;
@@ -880,7 +883,12 @@ mc_status svt_step(mc_handle h, mc_iter_info *out) {
   for (;;) {
     kk = std::min(k, std::max(1, k_cap));
     int pp = h->p;
-    clamp_kp(h, P.s, kk, pp);
+    if (P.inner == 1) {
+      int p1 = 0;  // rSVD-PI keeps one block of k + s columns whatever p
+      clamp_kp(h, P.s, kk, p1);
+    } else {
+      clamp_kp(h, P.s, kk, pp);
+    }
     bool width_ok = false;
     if (P.recycle == 1) width_ok = h->basis == 1 && h->q_real >= kk;
     if (P.recycle == 2) width_ok = h->basis == 2 && h->ub_k >= kk;
@@ -1049,6 +1057,7 @@ void mc_params_default(mc_params *p) {
   p->recycle = 1;
   p->k_max = 0;
   p->precision = 0;
+  p->inner = 0;
   p->seed = 0;
 }
 

@@ -1,7 +1,12 @@
 """Parity at the full rating workload the bench times: 138,000 x 27,000 with
 2e7 pairs (10 % held out for the SVT, 1.8e7 observed), against the oracle
-on the same inputs.  About a minute of oracle work on the host."""
+on the same inputs.  About a minute of oracle work on the host, plus the
+oracle's stored trajectory of the benchmark's SVT run
+(tests/golden/rating_svt_oracle.json, written from the oracle alone by
+tests/golden/make_rating_svt_oracle.py)."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -69,3 +74,60 @@ def test_svt_first_iterations_full_size(mc, rating):
     for a, b in zip(hist, ref.history):
         assert a["r"] == b["r"] and a["k"] == b["k"], (a, b)
         assert abs(a["err"] - b["err"]) <= 1e-4 * b["err"], (a, b)
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rating_svt_oracle.json")
+
+
+@pytest.fixture(scope="module")
+def stored():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def _heldout_rmse(h, o):
+    pred = h.sample(o.test_rows, o.test_cols).astype(np.float64)
+    return float(np.sqrt(np.mean((pred - o.test_val.astype(np.float64)) ** 2)))
+
+
+def test_svt_window_matches_stored_oracle(mc, rating, stored):
+    """The benchmark's SVT run (tau = 5n, delta = 1.9, warm-started Omega)
+    through every iteration the oracle stored (past the timed window, where
+    the rank is about 50): the same k, r and p at every iteration, the error
+    on Phi within 1e-4 (relative) of the oracle's, and the held-out RMSE of
+    X^i within 1e-3 of the oracle's wherever it was stored."""
+    o = rating
+    ref = stored["history"]
+    rmse = {int(k): v for k, v in stored["heldout_rmse"].items()}
+    assert ref[-1]["r"] >= 40 and rmse
+    prm = mc.params(**stored["params"])
+    worst = 0.0
+    with mc.Handle.from_observed(o) as h:
+        for b in ref:
+            a = h.svt_step(prm)
+            assert a["i"] == b["i"]
+            assert (a["k"], a["r"], a["p"]) == (b["k"], b["r"], b["p"]), (a, b)
+            assert abs(a["err"] - b["err"]) <= 1e-4 * b["err"], (a, b)
+            if b["i"] == 1:
+                assert a["c"] == b["c"]
+            if b["i"] in rmse:
+                d = abs(_heldout_rmse(h, o) - rmse[b["i"]])
+                worst = max(worst, d)
+                assert d <= 1e-3, (b["i"], d)
+    print(f"largest held-out RMSE difference from the oracle: {worst:.2e}")
+
+
+def test_svt_window_mixed_form_heldout_rmse(mc, rating, stored):
+    """The mixed-precision form (bf16 panels in the Krylov products) on the
+    same run: held-out RMSE within 1e-3 of the float64 oracle's at the last
+    stored iteration."""
+    o = rating
+    rmse = {int(k): v for k, v in stored["heldout_rmse"].items()}
+    last = max(rmse)
+    prm = mc.params(**stored["params"], precision=1)
+    with mc.Handle.from_observed(o) as h:
+        for _ in range(last):
+            info = h.svt_step(prm)
+        assert info["i"] == last
+        d = abs(_heldout_rmse(h, o) - rmse[last])
+    assert d <= 1e-3, d

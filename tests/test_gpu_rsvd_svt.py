@@ -178,6 +178,22 @@ def test_svt_iterate_matches_oracle_elementwise(mc, case):
                 assert np.linalg.norm(got - want) <= kw["delta"] * i * 1e-4 * m_fro, i
 
 
+def test_svt_inner_rsvd_pi_matches_oracle(mc):
+    """Alg. 6 with rSVD-PI (Alg. 4) as the inner SVD (mc_params.inner = 1),
+    warm-started Omega: the whole solve against the oracle's, iteration by
+    iteration."""
+    o = mc_synth.lowrank_uniform(500, 500, 10, frac=0.2, seed=0)
+    ref, hist, (Us, V, _) = _svt_compare(mc, o, dict(tau=2500.0, delta=6.0, eps=1e-4, recycle=3, seed=0, inner=1))
+    assert ref.converged and hist[-1]["converged"]
+    assert abs(len(hist) - ref.iters) <= 1
+    n = min(len(hist), ref.iters)
+    assert [x["r"] for x in hist[:n]] == [x["r"] for x in ref.history[:n]]
+    for a, b in zip(hist[:n], ref.history[:n]):
+        assert abs(a["err"] - b["err"]) <= 1e-4 * max(1.0, b["err"]), (a, b)
+    X = Us.astype(np.float64) @ V.astype(np.float64).T
+    assert np.linalg.norm(X - o.dense) / np.linalg.norm(o.dense) < 1e-3
+
+
 def test_svt_recycle_q_matches_oracle(mc):
     o = mc_synth.lowrank_uniform(500, 500, 10, frac=0.2, seed=0)
     ref, hist, _ = _svt_compare(mc, o, dict(tau=2500.0, delta=6.0, eps=1e-4, recycle=1, i_reuse=50, q_reuse=2,

@@ -167,6 +167,19 @@ def test_recycle_q_matches_alg2_on_config1(c1, c1_exact, c1_recycle_q):
     assert np.linalg.norm(X - Xe) / np.linalg.norm(Xe) < 1e-3
 
 
+def test_alg6_with_rsvd_pi_matches_alg2(c1, c1_exact):
+    """Alg. 6 with rSVD-PI (Alg. 4) as the SVD of each call reaches the exact
+    SVD's result on the rank-10 case: iteration count within 2, the same
+    recovered matrix."""
+    fa = svt.svt_fast(c1.m, c1.n, c1.row_ptr, c1.col, c1.val, tau=2500.0, delta=6.0, eps=1e-4, seed=0, recycle=3,
+                      inner=1)
+    ex = c1_exact
+    assert fa.converged and abs(fa.iters - ex.iters) <= 2
+    X, Xe = fa.Us @ fa.V.T, ex.Us @ ex.V.T
+    assert np.linalg.norm(X - Xe) / np.linalg.norm(Xe) < 1e-3
+    assert np.linalg.norm(X - c1.dense) / np.linalg.norm(c1.dense) < 1e-3
+
+
 def test_p_rule_on_error_sequence():
     """The p rule after Alg. 6 (Sec. IV.C) on a hand-written error sequence:
     +1 on every increase, -1 after ten strict decreases in a row, the streak
