@@ -361,6 +361,10 @@ def run_ours(args, rank, world, local):
         h.svt_step(prm)
     tm_all = h.timing_read()
     h.timing_enable(False)
+    # the ceiling of the products' gathers: the same panel rows in the same
+    # order with no arithmetic (mc_gather_rate), at the window's panel width
+    kb_w = 4 * ((window[-1]["k"] + S_OVER + 3) // 4)
+    gather_probe = {"csr": round(h.gather_rate(kb_w, trans=False), 1), "csc": round(h.gather_rate(kb_w, trans=True), 1)}
     h.close()
     oracle_rmse = None
     try:
@@ -401,6 +405,16 @@ def run_ours(args, rank, world, local):
                 "lts_pct_of_peak": tr.get("l2_throughput_pct_of_peak") if tr else None,
                 "l1_pct_of_peak": tr.get("l1_throughput_pct_of_peak") if tr else None,
                 "share_of_step": round(sp_ms / t_ms, 3) if t_ms > 0 else None}
+    gathered = {}
+    for cls, key in (("spmm", "csr"), ("spmm_t", "csc")):
+        c = tm[cls]
+        if c["ms"] > 0:
+            gathered[key] = round(c["launches"] * o.nnz * kb_w * 4 / 1e9 / (c["ms"] / 1e3), 1)
+    roofline["gather"] = {"panel_width": kb_w, "probe_gbs": gather_probe, "spmm_gathered_gbs": gathered,
+                          "frac_of_probe": {k: round(gathered[k] / gather_probe[k], 3) for k in gathered
+                                            if gather_probe.get(k)},
+                          "note": "gathered panel-row bytes per second of the products against the same gathers "
+                                  "alone (mc_gather_rate)"}
     # the fused update's fraction of HBM, from the per-class pass
     sd = tm_all["sddmm"]
     if sd["ms"] > 0 and sd["launches"] > 0:

@@ -356,6 +356,16 @@ mc_status mc_gram(int64_t R, int K, const float *X, float *G);
  * a TMA or MMA barrier expired. */
 mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G);
 
+/* mc_gather_rate: the rate (GB/s, gathered bytes) at which this GPU loads the
+ * panel rows the sparse products of Alg. 5 gather -- rows idx[e] of an
+ * n x k (trans = 0: the CSR column indices) or m x k (trans = 1: the CSC row
+ * indices) panel, k rounded up to 4, in the SpMM's 16-byte lane slices and
+ * entry order -- with no arithmetic or stores: the ceiling of the sparse
+ * products' gathers on this matrix.  k <= 128; reps timed launches after one
+ * warm-up (CUDA events on the handle's stream).  The paper has no counterpart
+ * (a measurement aid). */
+mc_status mc_gather_rate(mc_handle h, int trans, int k, int reps, double *gbs);
+
 /* mc_panel_gemm: Z = X W of a tall X (R x K, row-major) and a small W (K x N,
  * row-major) into Z (R x N, row-major): the panel products of the block
  * orthonormalisation (X R^{-1} of a CholeskyQR pass, X - Q_prev C of a

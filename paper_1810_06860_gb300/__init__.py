@@ -275,6 +275,13 @@ class Handle:
         return {name: dict(ms=t.ms, bytes=t.bytes, flops=t.flops, launches=t.launches)
                 for name, t in zip(_native.TIMING_NAMES, arr)}
 
+    def gather_rate(self, k: int, trans: bool = False, reps: int = 10) -> float:
+        """GB/s at which the sparse products' panel-row gathers alone run
+        (mc_gather_rate)."""
+        g = C.c_double(0.0)
+        _check(self._lib.mc_gather_rate(self._h, 1 if trans else 0, k, reps, C.byref(g)), "mc_gather_rate")
+        return g.value
+
     def spmm(self, X, trans: bool = False, device: bool = False):
         """Y X (trans=False, X: n x k) or Y^T X (trans=True, X: m x k)."""
         k = X.shape[1]

@@ -502,7 +502,7 @@ gemm_nn_kernel(int64_t R, int K1, int K2, const float *__restrict__ X, int ld_x,
 __global__ void __launch_bounds__(1024)
 chol_inv_small_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
                       float ref_tol, float *__restrict__ Rinv, const int *__restrict__ skip_if,
-                      int *__restrict__ set_skip) {
+                      int *__restrict__ set_skip, float skip3) {
   extern __shared__ float sh[];
   if (skip_if && *skip_if) return;  // a pass the previous one made unnecessary
   const int ls = (K % 2 == 0) ? K + 1 : K;  // odd row stride: column reads are conflict-free
@@ -550,7 +550,7 @@ chol_inv_small_kernel(int K, const float *__restrict__ G, int ld, float shift_re
     for (int off = 16; off > 0; off >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, off));
     if (lane == 0) atomicMax(&s_dev, __float_as_uint(dev));  // nonnegative floats order as their bits
     __syncthreads();
-    if (tid == 0) *set_skip = __uint_as_float(s_dev) < 1e-2f ? 1 : 0;
+    if (tid == 0) *set_skip = __uint_as_float(s_dev) <= skip3 ? 1 : 0;
   }
   __syncthreads();
   for (int j = 0; j < K; ++j) {
@@ -774,12 +774,12 @@ __global__ void select_cols_kernel(int K, const float *__restrict__ W, int ld_w,
 // repeated by every CTA (it is tiny), so its result needs no barrier.
 constexpr int ON_THREADS = 256;
 constexpr int ON_MAXK = 32;
-constexpr float ON_SKIP3 = 1e-2f;  // max |G - I| of the second pass that makes the third redundant
 
 struct OrthNarrowArgs {
   int64_t R, rows_per;
   int K, cols, ldx, ldq, ldo, use_ref;
   int q_smem;        // 1: rows of Qp staged in shared memory; 0: read from global (L2)
+  float skip3;       // max |G - I| of the second pass that makes the third redundant
   float *X;          // R x K (clobbered)
   const float *Qp;   // R x cols
   float *out;        // R x K
@@ -962,7 +962,7 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
 
   // CholeskyQR passes: X <- X R^{-1} with X^T X + shift I = R^T R, the first
   // shifted.  The third is skipped when the second pass's Gram is within
-  // ON_SKIP3 of the identity on its live columns: its input then has a
+  // skip3 of the identity on its live columns: its input then has a
   // condition number near 1, one pass leaves O(u) orthogonality (the
   // CholeskyQR2 bound) and a third would change nothing that matters.  Every
   // CTA reduces the same Gram in the same order, so all take the same branch.
@@ -1003,7 +1003,7 @@ __global__ void __launch_bounds__(ON_THREADS, KM <= 16 ? 2 : 1) orth_narrow_kern
             if (Ls[c * (K + 1) + c] > 0.5f) dev = fmaxf(dev, fabsf(Ls[lane * (K + 1) + c] - (c == lane ? 1.f : 0.f)));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) dev = fmaxf(dev, __shfl_xor_sync(full, dev, off));
-        if (lane == 0) s_skip3 = dev <= ON_SKIP3;
+        if (lane == 0) s_skip3 = dev <= a.skip3;
       }
       __syncwarp();
       const int rl = min(lane, K - 1);  // clamped indices: every load is in bounds, all issue at once
@@ -1246,6 +1246,16 @@ void gemm_nn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, in
   MC_CHECK_LAUNCH();
 }
 
+// The largest |G - I| of a CholeskyQR pass's Gram that makes the next pass
+// redundant (MC_SKIP3_TOL overrides).
+float skip3_tol() {
+  static const float v = [] {
+    const char *e = std::getenv("MC_SKIP3_TOL");
+    return e ? static_cast<float>(std::atof(e)) : 1e-2f;
+  }();
+  return v;
+}
+
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag, float ref_tol,
               float *Rinv, const int *skip_if, int *set_skip) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
@@ -1255,7 +1265,8 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
     constexpr size_t kMax = sizeof(float) * (2 * 128 * 129 + 128);  // K = 128; fixed for concurrent callers
     MC_CUDA(cudaFuncSetAttribute(chol_inv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax));
     const int threads = K <= 32 ? 256 : (K <= 64 ? 512 : 1024);
-    chol_inv_small_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip);
+    chol_inv_small_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip,
+                                                    skip3_tol());
     MC_CHECK_LAUNCH();
     return;
   }
@@ -1332,6 +1343,7 @@ bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const flo
     if ((int64_t)occ * sms < nb) continue;
     const int64_t stride = on_stride(K, cols);
     OrthNarrowArgs a{};
+    a.skip3 = skip3_tol();
     a.R = R;
     a.rows_per = rows_per;
     a.K = K;

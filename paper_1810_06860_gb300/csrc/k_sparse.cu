@@ -852,6 +852,42 @@ void mirror_values(cudaStream_t st, int64_t nnz, const int *perm, const float *y
   MC_CHECK_LAUNCH();
 }
 
+// ---- gather probe ------------------------------------------------------------
+// The SpMM's panel-row gathers alone: a warp walks a contiguous chunk of an
+// index stream (the CSR column or CSC row indices, in the product's entry
+// order), its lane groups taking alternate entries as in spmm_seg_kernel, and
+// each lane loads its 16-byte slices of the indexed row, with no products,
+// partials or stores; a per-thread sum keeps the loads live.  Its rate is the
+// ceiling for the product's gathers on the same matrix and panel width.
+__global__ void __launch_bounds__(256)
+gather_probe_kernel(int64_t nnz, const int *__restrict__ idx, const float4 *__restrict__ P, int ld4, int K4, int L,
+                    float *__restrict__ sink) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t w = tid >> 5;
+  const int lane = static_cast<int>(tid & 31), grp = lane / L, sub = lane % L, ngrp = 32 / L;
+  const int64_t chunk = (nnz + nwarps - 1) / nwarps;
+  const int64_t e0 = w * chunk, e1 = min(nnz, e0 + chunk);
+  float acc = 0.f;
+  for (int64_t e = e0 + grp; e < e1; e += ngrp) {
+    const float4 *row = P + (int64_t)__ldg(idx + e) * ld4;
+    for (int q = sub; q < K4; q += L) {
+      const float4 v = __ldg(row + q);
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  }
+  sink[tid] = acc;
+}
+
+void gather_probe(cudaStream_t st, int64_t nnz, const int *idx, const float *P, int ldp, int K, float *sink,
+                  int grid) {
+  const int K4 = (K + 3) / 4;
+  int L = 1;
+  while (L < K4 && L < 32) L <<= 1;
+  gather_probe_kernel<<<grid, 256, 0, st>>>(nnz, idx, reinterpret_cast<const float4 *>(P), ldp / 4, K4, L, sink);
+  MC_CHECK_LAUNCH();
+}
+
 int sddmm_update(cudaStream_t st, int64_t nnz, const int *rix, const int *col, const float *mval, float *y,
                  const float *Us, int ld_us, const float *V, int ld_v, int r, float delta, int update, double *block_sq,
                  float *x_out) {

@@ -1371,6 +1371,38 @@ mc_status mc_svt_sample(mc_handle h, int64_t count, const int64_t *rows, const i
   });
 }
 
+mc_status mc_gather_rate(mc_handle h, int trans, int k, int reps, double *gbs) {
+  if (!h || !gbs || k < 1 || k > 128 || reps < 1) return MC_EINVAL;
+  return guarded([&]() -> mc_status {
+    const int kp = (int)round_up(k, 4);
+    const int64_t rows_in = trans ? h->m : h->n;
+    const int *idx = trans ? h->ri.as<int>() : h->ci.as<int>();
+    int dev = 0, sms = 0;
+    MC_CUDA(cudaGetDevice(&dev));
+    MC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = sms * 8;
+    DBuf dp, ds;
+    BufGuard g(h->alloc, {&dp, &ds});
+    dp.reserve(h->alloc, sizeof(float) * rows_in * kp);
+    ds.reserve(h->alloc, sizeof(float) * (size_t)grid * 256);
+    MC_CUDA(cudaMemsetAsync(dp.p, 0, sizeof(float) * rows_in * kp, h->stream));
+    cudaEvent_t e0, e1;
+    MC_CUDA(cudaEventCreate(&e0));
+    MC_CUDA(cudaEventCreate(&e1));
+    gather_probe(h->stream, h->nnz, idx, dp.as<float>(), kp, kp, ds.as<float>(), grid);  // warm-up
+    MC_CUDA(cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < reps; ++r) gather_probe(h->stream, h->nnz, idx, dp.as<float>(), kp, kp, ds.as<float>(), grid);
+    MC_CUDA(cudaEventRecord(e1, h->stream));
+    MC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *gbs = ms > 0.f ? (double)h->nnz * kp * 4.0 * reps / (ms * 1e-3) / 1e9 : 0.0;
+    return MC_OK;
+  });
+}
+
 mc_status mc_spmm(mc_handle h, int trans, int k, const float *X, float *out) {
   if (!h || k < 1 || !X || !out) return MC_EINVAL;
   return guarded([&]() -> mc_status {

@@ -161,6 +161,11 @@ int sddmm_update(cudaStream_t st, int64_t nnz, const int *rix, const int *col, c
                  const float *Us, int ld_us, const float *V, int ld_v, int r, float delta, int update,
                  double *block_sq, float *x_out);
 int sddmm_partials();
+// The SpMM's gathers alone (k_sparse.cu): rows idx[e] of the panel P (ldp a
+// multiple of 4, K columns) loaded in 16-byte slices by lane groups, summed
+// into sink (grid * 256 floats); the ceiling for the SpMM's gathers.
+void gather_probe(cudaStream_t st, int64_t nnz, const int *idx, const float *P, int ldp, int K, float *sink,
+                  int grid);
 // rix[e] = row of CSR entry e.
 void expand_rows(cudaStream_t st, int64_t m, const int *rp, int *rix);
 // Deterministic sum of a double array into out[0] (one block, fixed order).

@@ -263,3 +263,15 @@ def test_panel_gemm_tensor_cores_rejects_wide(mc):
     W = np.zeros((256, 128), np.float32)  # 256 x 128 > 16384
     with pytest.raises(mc.McError):
         mc.panel_gemm(X, W, tensor_cores=True)
+
+
+def test_gather_rate_probe(mc):
+    """mc_gather_rate runs the products' gathers alone and reports a positive
+    rate for both index streams; bad arguments are rejected."""
+    o = mc_synth.ratings(m=4000, n=1500, N=150000, seed=2)
+    with mc.Handle.from_observed(o) as h:
+        for trans in (False, True):
+            g = h.gather_rate(60, trans=trans, reps=3)
+            assert np.isfinite(g) and g > 0
+        with pytest.raises(mc.McError):
+            h.gather_rate(256)
