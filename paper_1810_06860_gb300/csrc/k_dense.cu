@@ -1177,14 +1177,12 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
   MC_CHECK_LAUNCH();
 }
 
-// The tensor-core panel product is opt-in (MC_NN_TC=1): with W's hi and lo
-// copies resident in shared memory too few X boxes stay in flight per SM, and
-// it measured no faster than the SIMT kernels (equal at K = 60, slower at
-// K = 180 and 240).
+// Panel products with more than 16 output columns run on the tensor cores
+// (k_tc.cu) where the shape fits; MC_NN_TC=0 keeps the SIMT kernels.
 bool use_nn_tc() {
   static const bool on = [] {
     const char *v = std::getenv("MC_NN_TC");
-    return v && v[0] == '1';
+    return !(v && v[0] == '0');
   }();
   return on;
 }

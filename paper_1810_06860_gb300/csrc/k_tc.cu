@@ -5,7 +5,7 @@
 // One CTA of 128 threads per row range.  TMA loads 32-row stages of the panel
 // as 32-column boxes (128-byte rows, 128-byte swizzle) into a double-buffered
 // shared-memory ring.  The threads split every value into a TF32 "hi" part
-// (low 13 mantissa bits cleared) and the float32 remainder "lo" and write both
+// and a TF32 remainder "lo" (both rounded to nearest) and write both
 // transposed into the K-major 128-byte-swizzled operand layout (the panel's
 // rows are the reduction dimension; a 32-row stage is exactly one 128-byte
 // swizzle row per panel column).  One thread issues tcgen05.mma kind::tf32 and
@@ -128,6 +128,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Split of a float32 value for 3xTF32 products: hi is the value rounded to
+// the nearest TF32 number (10-bit mantissa, ties away from zero), the
+// remainder x - hi is exact in float32 and is rounded the same way, so
+// hi + lo carries x to about 2^-24 relative, as float32 does (truncating both
+// parts would leave 2^-22).
+__device__ __forceinline__ float tf32_rn(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ void tf32_split(float x, float &h, float &l) {
+  h = tf32_rn(x);
+  l = tf32_rn(x - h);
+}
+
 struct TcSmem {
   // 1024-byte aligned ring: raw / hi / lo, two stages each, boxes of 4 KiB
   static constexpr size_t stage_bytes = (size_t)TC_MAX_BOXES * TC_BOX_BYTES;  // 32 KiB
@@ -208,9 +221,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
       for (int u = 0; u < 4; ++u) {
         const int c = c0 + u;
         const int off = (c >> 3) * 256 + (c & 7) * 32 + ((((r >> 2) ^ (c & 7)) & 7) << 2) + (r & 3);
-        const float h = __uint_as_float(__float_as_uint(vals[u]) & 0xFFFFE000u);
+        float h, l;
+        tf32_split(vals[u], h, l);
         dh[off] = h;
-        dl[off] = vals[u] - h;
+        dl[off] = l;
       }
     }
     fence_proxy_async();
@@ -321,64 +335,86 @@ gram_tc_reduce_kernel(int K, int nsplit, const float *__restrict__ partial, int 
 // ---- panel times small factor on the tensor cores ---------------------------
 // Z (R x N) = alpha X (R x K) W (K x N) diag(colscale) + beta Z, float32 in and
 // out, for K_p N_p <= 16384 (K_p = K rounded up to 32, N_p = N rounded up to
-// 32): the block products of the Krylov orthonormalisation (X R^{-1},
+// 16): the block products of the Krylov orthonormalisation (X R^{-1},
 // X - Q_prev C) and the Ritz factors U = Q W, V = B^T W S^{-1} (Alg. 5 step
-// 11, Alg. 3 step 4).
-//
-// One CTA of 128 threads per SM walks 128-row tiles of X.  TMA brings each
-// tile in 32-column boxes (128-byte rows, 128-byte swizzle), which is already
-// the K-major operand layout of tcgen05.mma; the threads split each box in
-// place into a TF32 "hi" part and a float32 remainder "lo".  W, staged once per
-// CTA, is written transposed into the same layout (hi and lo).  One thread
-// issues hi*hi + hi*lo + lo*hi per 8-column k-step into a 128 x N_p float32
-// accumulator in tensor memory (about float32 accuracy); a box's stage is
-// reloaded once the MMAs reading it have completed.  After the last box of a
-// tile each warp reads its 32 accumulator rows (tcgen05.ld) and writes the
-// epilogue.  Every mbarrier wait is bounded; on expiry the kernel records an
-// error code, waits (bounded) for its outstanding copies and MMAs, frees its
-// tensor memory and returns.
-constexpr int NT_THREADS = 128, NT_BM = 128, NT_KC = 32;
+// 11, Alg. 3 step 4).  TMA brings 128-row x 32-column boxes of X (128-byte
+// rows, 128-byte swizzle), which is already the K-major operand layout of
+// tcgen05.mma; W, staged once per CTA, is written transposed into the same
+// layout as hi and lo parts; the product accumulates hi*hi + hi*lo + lo*hi in
+// float32 in tensor memory (about float32 accuracy).
+constexpr int NT_BM = 128, NT_KC = 32;
 constexpr int NT_BOX_BYTES = NT_BM * NT_KC * 4;  // 16 KiB
 constexpr int NT_MAX_W = 16384;                   // K_p * N_p floats
 constexpr size_t NT_SMEM_LIMIT = 220 * 1024;
 
-__global__ void __launch_bounds__(NT_THREADS, 2)
-gemm_nn_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int N, int Kp, int Np,
-                  uint32_t tmem_cols, int nst, const float *__restrict__ W, int ld_w,
-                  const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z, int ld_z,
-                  int *__restrict__ err, const int *__restrict__ copy_if, int ld_x, const float *__restrict__ Xp) {
-  extern __shared__ __align__(1024) uint8_t nt_raw_smem[];
+// The kernel is warp-specialised: 384 threads in roles that hand boxes to each other through mbarriers:
+//   warp 0, lane 0   TMA producer: loads box g into stage g % nst once the
+//                    MMAs of box g - nst released it;
+//   warp 1, lane 0   MMA issuer: hi*hi + hi*lo + lo*hi per 8-column step into
+//                    one of two TMEM accumulators (tiles alternate), releases
+//                    the stage (commit) and, after a tile's last box, hands
+//                    the accumulator to the epilogue (commit);
+//   warps 4..7       split each landed box in place into TF32 hi and float32
+//                    lo and signal the issuer;
+//   warps 8..11      epilogue: each reads its 32 accumulator rows (tcgen05.ld,
+//                    lanes 32 (w % 4) ..), stages 32 columns at a time in its
+//                    own shared memory and writes whole rows with float4
+//                    stores, then frees the accumulator.
+// So the split of box g + 1, the MMAs of box g and the epilogue of the
+// previous tile run at the same time.  Every wait is bounded: an expiry sets
+// a shared failure flag that ends every role's loop; each role then waits
+// (bounded) for its own outstanding copies or MMAs before the block frees its
+// tensor memory.
+constexpr int NW_THREADS = 384;
+constexpr int NW_MAXST = 4;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool failed(const volatile int *f) { return *f != 0; }
+
+__global__ void __launch_bounds__(NW_THREADS, 1)
+gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int N, int Kp, int Np,
+                     uint32_t tmem_cols, int nst, const float *__restrict__ W, int ld_w,
+                     const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z, int ld_z,
+                     int *__restrict__ err, const int *__restrict__ copy_if, int ld_x, const float *__restrict__ Xp) {
+  extern __shared__ __align__(1024) uint8_t nw_raw_smem[];
+  __shared__ __align__(8) uint64_t full_bar[NW_MAXST], split_bar[NW_MAXST], empty_bar[NW_MAXST];
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int s_fail;
   if (copy_if && *copy_if) {
-    // copy mode (the factor is the identity: a pass the previous one made
-    // unnecessary): Z = X, K == N
-    for (int64_t e = blockIdx.x * (int64_t)NT_THREADS + threadIdx.x; e < R * K; e += (int64_t)gridDim.x * NT_THREADS) {
+    // copy mode (the factor is the identity): Z = X, K == N
+    for (int64_t e = blockIdx.x * (int64_t)NW_THREADS + threadIdx.x; e < R * K; e += (int64_t)gridDim.x * NW_THREADS) {
       const int64_t r = e / K;
       const int c = static_cast<int>(e % K);
       Z[r * ld_z + c] = Xp[r * ld_x + c];
     }
     return;
   }
-  __shared__ __align__(8) uint64_t full_bar[4];
-  __shared__ __align__(8) uint64_t mma_bar[4];
-  __shared__ __align__(8) uint64_t acc_bar;
-  __shared__ uint32_t tmem_base_sh;
-  __shared__ int s_fail;  // failure codes, for the report only (control uses barrier votes)
-  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(nt_raw_smem) + 1023) & ~uintptr_t(1023));
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(nw_raw_smem) + 1023) & ~uintptr_t(1023));
   const int kchunks = Kp / NT_KC;
-  const size_t wbytes = (size_t)Kp * Np * 4;  // one of hi / lo
+  const size_t wbytes = (size_t)Kp * Np * 4;
   uint8_t *whi = base, *wlo = base + wbytes;
-  uint8_t *stg = base + 2 * wbytes;           // nst stages of (hi, lo) boxes
+  uint8_t *stg = base + 2 * wbytes;                                         // nst x (hi, lo) boxes
+  float *epi = reinterpret_cast<float *>(stg + (size_t)nst * 2 * NT_BOX_BYTES);  // 4 warps x 32 x 32 floats
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (R + NT_BM - 1) / NT_BM;
   const int my_tiles = blockIdx.x < ntiles ? static_cast<int>((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-  const int G = my_tiles * kchunks;           // boxes this CTA consumes
+  const int G = my_tiles * kchunks;
+  volatile int *vfail = &s_fail;
 
   if (tid == 0) {
     for (int s = 0; s < nst; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&mma_bar[s], 1);
+      mbar_init(&split_bar[s], 4);   // one arrival per split warp
+      mbar_init(&empty_bar[s], 1);   // MMA commit
     }
-    mbar_init(&acc_bar, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf_bar[a], 1);    // MMA commit
+      mbar_init(&acce_bar[a], 4);    // one arrival per epilogue warp
+    }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -390,15 +426,16 @@ gemm_nn_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, in
   // W^T (N_p x K_p, K-major, 128-byte swizzle) as hi and lo: element (n, k) of
   // column block kc at kc * N_p * 128 + (n / 8) * 1024 + (n % 8) * 128 +
   // (((k % 32) / 4) ^ (n % 8)) * 16 + (k % 4) * 4
-  for (int k = wid; k < Kp; k += NT_THREADS / 32) {  // a warp per row of W, lanes along it
+  for (int k = wid; k < Kp; k += NW_THREADS / 32) {
     const int kc = k / NT_KC, kl = k % NT_KC;
     for (int n = lane; n < Np; n += 32) {
       const float w = (k < K && n < N) ? W[(int64_t)k * ld_w + n] : 0.f;
-      const float h = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
+      float h, lw;
+      tf32_split(w, h, lw);
       const size_t off =
           (size_t)kc * Np * 128 + (n >> 3) * 1024 + (n & 7) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
       *reinterpret_cast<float *>(whi + off) = h;
-      *reinterpret_cast<float *>(wlo + off) = w - h;
+      *reinterpret_cast<float *>(wlo + off) = lw;
     }
   }
   fence_proxy_async();
@@ -406,112 +443,130 @@ gemm_nn_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, in
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
-
   auto box_hi = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES; };
   auto box_lo = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES + NT_BOX_BYTES; };
-  auto issue = [&](int g) {
-    const int s = g % nst;
-    const int tl = g / kchunks, kc = g % kchunks;
-    const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
-    mbar_expect_tx(&full_bar[s], NT_BOX_BYTES);
-    tma_load_2d(box_hi(s), &xmap, kc * NT_KC, static_cast<int>(tile * NT_BM), &full_bar[s]);
-  };
-  // only tid 0 issues copies and MMAs, so it alone tracks how far both got
-  int issued = 0, committed = -1;
-  if (tid == 0)
-    for (; issued < G && issued < nst; ++issued) issue(issued);
-  const uint32_t idesc = idesc_tf32(NT_BM, Np);
-  const bool vec_out = ld_z % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15u) == 0;
-  const uint32_t wstride = static_cast<uint32_t>(Np) * 128;
-  int lf = 0;  // this thread saw a wait expire
-  for (int g = 0; g < G; ++g) {
-    const int s = g % nst, kc = g % kchunks, tl = g / kchunks;
-    if (!mbar_wait(&full_bar[s], (g / nst) & 1)) {
-      lf = 1;
-      atomicOr(&s_fail, 1);
-    }
-    // split the box in place: hi stays, lo goes to the stage's second box
-    float4 *hi4 = reinterpret_cast<float4 *>(box_hi(s));
-    float4 *lo4 = reinterpret_cast<float4 *>(box_lo(s));
-    for (int q = tid; q < NT_BOX_BYTES / 16; q += NT_THREADS) {
-      const float4 v = hi4[q];
-      float4 h, l;
-      h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-      h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-      h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-      h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-      l.x = v.x - h.x;
-      l.y = v.y - h.y;
-      l.z = v.z - h.z;
-      l.w = v.w - h.w;
-      hi4[q] = h;
-      lo4[q] = l;
-    }
-    fence_proxy_async();
-    if (__syncthreads_or(lf)) break;  // a block-wide vote: every thread leaves together
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t ah = smem_u32(box_hi(s)), al = smem_u32(box_lo(s));
-      const uint32_t bh = smem_u32(whi) + kc * wstride, bl = smem_u32(wlo) + kc * wstride;
-#pragma unroll
-      for (int ks = 0; ks < NT_KC / 8; ++ks) {
-        const uint32_t ko = ks * 32;
-        const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, acc0);
-        mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
-        mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
-      }
-      mma_commit(&mma_bar[s]);
-      committed = g;
-      if (kc == kchunks - 1) mma_commit(&acc_bar);
-      // refill the stage of the previous box once its MMAs have read it
-      if (g >= 1 && issued < G) {
-        const int gp = g - 1;
-        if (mbar_wait(&mma_bar[gp % nst], (gp / nst) & 1)) {
-          issue(issued);
-          ++issued;
-        } else {
-          lf = 1;
-          atomicOr(&s_fail, 2);
+  const unsigned fullm = 0xffffffffu;
+  if (wid == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      int issued = 0;
+      for (int g = 0; g < G; ++g) {
+        if (failed(vfail)) break;
+        const int s = g % nst;
+        if (g >= nst && !mbar_wait(&empty_bar[s], ((g / nst) - 1) & 1)) {
+          atomicOr(&s_fail, 1);
+          break;
         }
+        const int tl = g / kchunks, kc = g % kchunks;
+        const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
+        mbar_expect_tx(&full_bar[s], NT_BOX_BYTES);
+        tma_load_2d(box_hi(s), &xmap, kc * NT_KC, static_cast<int>(tile * NT_BM), &full_bar[s]);
+        issued = g + 1;
       }
+      // every issued copy lands before the block exits: the last one per stage
+      // is the latest phase armed there (a completed one returns at once)
+      for (int g = max(0, issued - nst); g < issued; ++g) mbar_wait(&full_bar[g % nst], (g / nst) & 1);
     }
-    if (kc == kchunks - 1) {
-      // epilogue of the tile: wait for its MMAs, then each warp its 32 rows
-      if (!mbar_wait(&acc_bar, tl & 1)) {
-        lf = 1;
-        atomicOr(&s_fail, 4);
+  } else if (wid == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(NT_BM, Np);
+      const uint32_t wstride = static_cast<uint32_t>(Np) * 128;
+      int committed = -1;
+      for (int g = 0; g < G; ++g) {
+        if (failed(vfail)) break;
+        const int s = g % nst, tl = g / kchunks, kc = g % kchunks, a = tl & 1;
+        if (kc == 0 && tl >= 2 && !mbar_wait(&acce_bar[a], ((tl >> 1) - 1) & 1)) {
+          atomicOr(&s_fail, 2);
+          break;
+        }
+        if (!mbar_wait(&split_bar[s], (g / nst) & 1)) {
+          atomicOr(&s_fail, 4);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + static_cast<uint32_t>(a * Np);
+        const uint32_t ah = smem_u32(box_hi(s)), al = smem_u32(box_lo(s));
+        const uint32_t bh = smem_u32(whi) + kc * wstride, bl = smem_u32(wlo) + kc * wstride;
+#pragma unroll
+        for (int ks = 0; ks < NT_KC / 8; ++ks) {
+          const uint32_t ko = ks * 32;
+          const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(d, smem_desc(ah + ko), smem_desc(bh + ko), idesc, acc0);
+          mma_tf32(d, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
+          mma_tf32(d, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
+        }
+        mma_commit(&empty_bar[s]);
+        if (kc == kchunks - 1) mma_commit(&accf_bar[a]);
+        committed = g;
       }
-      const bool ok = !__syncthreads_or(lf);  // block-uniform
+      // the last commit covers every MMA issued before it
+      if (committed >= 0 && !mbar_wait(&empty_bar[committed % nst], (committed / nst) & 1)) atomicOr(&s_fail, 64);
+    }
+  } else if (wid >= 4 && wid < 8) {
+    // ---- split into TF32 hi (in place) and float32 lo ----
+    const int st = tid - 128;
+    for (int g = 0; g < G; ++g) {
+      if (__any_sync(fullm, failed(vfail))) break;
+      const int s = g % nst;
+      const bool ok = mbar_wait(&full_bar[s], (g / nst) & 1);
+      if (!__all_sync(fullm, ok)) {
+        atomicOr(&s_fail, 8);
+        break;
+      }
+      float4 *hi4 = reinterpret_cast<float4 *>(box_hi(s));
+      float4 *lo4 = reinterpret_cast<float4 *>(box_lo(s));
+#pragma unroll 4
+      for (int q = st; q < NT_BOX_BYTES / 16; q += 128) {
+        const float4 v = hi4[q];
+        float4 h, l;
+        tf32_split(v.x, h.x, l.x);
+        tf32_split(v.y, h.y, l.y);
+        tf32_split(v.z, h.z, l.z);
+        tf32_split(v.w, h.w, l.w);
+        hi4[q] = h;
+        lo4[q] = l;
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&split_bar[s]);
+    }
+  } else if (wid >= 8) {
+    // ---- epilogue: accumulator rows 32 (w % 4) .. + 31 of each tile ----
+    const int ew = wid - 8;
+    float4 *buf4 = reinterpret_cast<float4 *>(epi) + ew * 32 * 8;  // 32 rows x 8 float4
+    const bool vec_out = ld_z % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15u) == 0;
+    for (int tl = 0; tl < my_tiles; ++tl) {
+      if (__any_sync(fullm, failed(vfail))) break;
+      const int a = tl & 1;
+      const bool ok = mbar_wait(&accf_bar[a], (tl >> 1) & 1);
+      if (!__all_sync(fullm, ok)) {
+        atomicOr(&s_fail, 16);
+        break;
+      }
       tc_fence_after();
-      // 64 columns at a time: each thread moves its accumulator row into the
-      // stage of the box just consumed (free once the MMAs are done; its
-      // refill is issued in the next iteration), float4 chunk q of row r at
-      // q ^ (r % 16); then the block writes whole rows with float4 stores
-      float4 *tile_out = reinterpret_cast<float4 *>(box_hi(s));  // 128 rows x 16 float4
-      const int64_t row0 = ((int64_t)blockIdx.x + (int64_t)tl * gridDim.x) * NT_BM;
-      const int r = 32 * wid + lane;
-      for (int c0 = 0; ok && c0 < N; c0 += 64) {
-        for (int c = 0; c < 64 && c0 + c < N; c += 16) {
+      const int64_t row0 = ((int64_t)blockIdx.x + (int64_t)tl * gridDim.x) * NT_BM + 32 * ew;
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        for (int c = 0; c < 32 && c0 + c < N; c += 16) {
           float v[16];
-          tmem_ld16(tmem + (static_cast<uint32_t>(32 * wid) << 16) + c0 + c, v);
+          tmem_ld16(tmem + (static_cast<uint32_t>(32 * ew) << 16) + static_cast<uint32_t>(a * Np + c0 + c), v);
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            tile_out[r * 16 + (((c >> 2) + u) ^ (r & 15))] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            buf4[lane * 8 + (((c >> 2) + u) ^ (lane & 7))] =
+                make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
         }
-        __syncthreads();
-        const int ncol = min(64, N - c0);
-        for (int e = tid; e < NT_BM * 16; e += NT_THREADS) {
-          const int rr = e >> 4, q = e & 15, col = 4 * q;
+        __syncwarp();
+        for (int e = lane; e < 32 * 8; e += 32) {
+          const int rr = e >> 3, q = e & 7, col = c0 + 4 * q;
           const int64_t grow = row0 + rr;
-          if (grow >= R || col >= ncol) continue;
-          const float4 v4 = tile_out[rr * 16 + (q ^ (rr & 15))];
+          if (grow >= R || col >= N) continue;
+          const float4 v4 = buf4[rr * 8 + (q ^ (rr & 7))];
           const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-          float *z = Z + grow * ld_z + c0 + col;
-          if (vec_out && col + 3 < ncol) {
+          float *z = Z + grow * ld_z + col;
+          if (vec_out && col + 3 < N) {
             float o[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) o[i] = vv[i] * alpha * (colscale ? colscale[c0 + col + i] : 1.0f);
+            for (int i = 0; i < 4; ++i) o[i] = vv[i] * alpha * (colscale ? colscale[col + i] : 1.0f);
             if (beta != 0.f) {
               const float4 zo = *reinterpret_cast<const float4 *>(z);
               o[0] += beta * zo.x;
@@ -521,28 +576,21 @@ gemm_nn_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, in
             }
             *reinterpret_cast<float4 *>(z) = make_float4(o[0], o[1], o[2], o[3]);
           } else {
-            for (int i = 0; i < 4 && col + i < ncol; ++i)
-              z[i] = (beta != 0.f ? beta * z[i] : 0.f) + vv[i] * alpha * (colscale ? colscale[c0 + col + i] : 1.0f);
+            for (int i = 0; i < 4 && col + i < N; ++i)
+              z[i] = (beta != 0.f ? beta * z[i] : 0.f) + vv[i] * alpha * (colscale ? colscale[col + i] : 1.0f);
           }
         }
-        __syncthreads();
+        __syncwarp();
       }
       tc_fence_before();
-      __syncthreads();  // the accumulator is read before the next tile's first MMA
-      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[a]);
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    // after an early exit: wait for the last committed MMAs and for the
-    // copies that no MMA consumed (bounded waits; a completed phase returns at once)
-    if (committed >= 0 && !mbar_wait(&mma_bar[committed % nst], (committed / nst) & 1)) atomicOr(&s_fail, 8);
-    for (int t = committed + 1; t < issued; ++t) mbar_wait(&full_bar[t % nst], (t / nst) & 1);
-  }
-  tc_fence_before();
-  __syncthreads();
+  tc_fence_after();
   if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
-  if (tid == 0 && s_fail && err) atomicOr(err, s_fail << 4);
+  if (tid == 0 && s_fail && err) atomicOr(err, s_fail << 8);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -569,37 +617,23 @@ int tc_nsplit(int64_t R) {
 // ---- panel x small factor (tensor cores) --------------------------------------
 namespace {
 struct NtPlan {
-  int Kp, Np, nst, ctas;
+  int Kp, Np, nst;
   uint32_t cols;
   size_t smem;
 };
-// CTAs per SM: two when W and two stages fit in half the shared memory
-// (MC_NT_CTAS=1 keeps one CTA with up to four stages).
-int nt_ctas_pref() {
-  static const int v = [] {
-    const char *e = std::getenv("MC_NT_CTAS");
-    return (e && e[0] == '1') ? 1 : 2;
-  }();
-  return v;
-}
-
+// W's hi and lo parts, a 16 KiB epilogue tile and as many (hi, lo) box stages
+// as fit (two to four); two accumulators of N_p columns in tensor memory
 NtPlan nt_plan(int K, int N) {
   NtPlan p{};
   p.Kp = static_cast<int>(round_up(K, NT_KC));
   p.Np = static_cast<int>(round_up(N, 16));
-  const size_t wbytes = (size_t)p.Kp * p.Np * 4;
-  const size_t half = 110 * 1024;
-  p.ctas = 1;
-  size_t limit = NT_SMEM_LIMIT;
-  if (nt_ctas_pref() == 2 && 2 * wbytes + 2 * 2 * NT_BOX_BYTES + 1024 <= half) {
-    p.ctas = 2;
-    limit = half;
-  }
-  const size_t avail = limit > 2 * wbytes + 1024 ? limit - 2 * wbytes - 1024 : 0;
-  p.nst = static_cast<int>(std::min<size_t>(4, avail / (2 * NT_BOX_BYTES)));
-  p.smem = 2 * wbytes + (size_t)p.nst * 2 * NT_BOX_BYTES + 1024;
+  const size_t fixed = 2 * (size_t)p.Kp * p.Np * 4 + 16 * 1024 + 1024;
+  p.nst = fixed < NT_SMEM_LIMIT ? static_cast<int>(std::min<size_t>(NW_MAXST, (NT_SMEM_LIMIT - fixed) /
+                                                                                     (2 * NT_BOX_BYTES)))
+                                : 0;
+  p.smem = fixed + (size_t)p.nst * 2 * NT_BOX_BYTES;
   p.cols = 32;
-  while (p.cols < static_cast<uint32_t>(p.Np)) p.cols <<= 1;
+  while (p.cols < static_cast<uint32_t>(2 * p.Np)) p.cols <<= 1;
   return p;
 }
 }  // namespace
@@ -632,10 +666,11 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
     MC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
   const int64_t ntiles = (R + NT_BM - 1) / NT_BM;
-  const int grid = static_cast<int>(std::min<int64_t>(ntiles, (int64_t)sms * p.ctas));
-  MC_CUDA(cudaFuncSetAttribute(gemm_nn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NT_SMEM_LIMIT));
-  gemm_nn_tc_kernel<<<grid, NT_THREADS, p.smem, st>>>(map, R, K, N, p.Kp, p.Np, p.cols, p.nst, W, ld_w, colscale,
-                                                       alpha, beta, Z, ld_z, err, copy_if, ld_x, X);
+  const int grid = static_cast<int>(std::min<int64_t>(ntiles, sms));
+  MC_CUDA(cudaFuncSetAttribute(gemm_nn_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)NT_SMEM_LIMIT));
+  gemm_nn_tc_ws_kernel<<<grid, NW_THREADS, p.smem, st>>>(map, R, K, N, p.Kp, p.Np, p.cols, p.nst, W, ld_w, colscale,
+                                                          alpha, beta, Z, ld_z, err, copy_if, ld_x, X);
   MC_CHECK_LAUNCH();
 }
 

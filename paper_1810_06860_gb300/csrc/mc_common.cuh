@@ -188,7 +188,7 @@ void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_
 // Z (R x K2, ld_z) = beta * Z + alpha * X (R x K1, ld_x) * W (K1 x K2, ld_w) * diag(colscale)
 // colscale may be NULL (ones).  Z may not alias X.  copy_if (device int, may
 // be NULL; 16 < K1 == K2 <= 64 only): when it holds a nonzero value, Z = X.
-// With MC_NN_TC=1 the shapes the tensor-core kernel takes (K2 > 16) run there;
+// Shapes the tensor-core kernel takes (K2 > 16) run there unless MC_NN_TC=0;
 // err (device int, may be NULL) receives its wait-expiry code.
 void gemm_nn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *W,
              int ld_w, const float *colscale, float alpha, float beta, float *Z, int ld_z,
