@@ -356,6 +356,16 @@ mc_status mc_gram(int64_t R, int K, const float *X, float *G);
  * a TMA or MMA barrier expired. */
 mc_status mc_gram_tc(int64_t R, int K, const float *X, float *G);
 
+/* mc_panel_gram: C = X1^T X2 (K1 x K2, row-major) of two tall panels X1 (R x
+ * K1) and X2 (R x K2), row-major: the Grams of the block orthonormalisation
+ * and the Ritz Gram B B^T (Alg. 3 step 1, Alg. 5 steps 3-9) and the
+ * projections Q_prev^T X.  tensor_cores = 1 runs the tcgen05 kernel (TF32
+ * operands split into hi and lo parts, float32 accumulation; K1, K2 <= 256,
+ * else MC_EINVAL with nothing run); 0 runs the SIMT kernels.  Host or device
+ * pointers; synchronous; MC_ETIMEOUT if a bounded wait of the tensor-core
+ * kernel expired. */
+mc_status mc_panel_gram(int64_t R, int K1, int K2, const float *X1, const float *X2, float *C, int tensor_cores);
+
 /* mc_gather_rate: the rate (GB/s, gathered bytes) at which this GPU loads the
  * panel rows the sparse products of Alg. 5 gather -- rows idx[e] of an
  * n x k (trans = 0: the CSR column indices) or m x k (trans = 1: the CSC row

@@ -337,6 +337,19 @@ def panel_gemm(X, W, tensor_cores: bool = True):
     return Z
 
 
+def panel_gram(X1, X2, tensor_cores: bool = True):
+    """C = X1^T X2 of two tall float32 panels with the same row count (mc_panel_gram)."""
+    lib = load()
+    X1 = np.ascontiguousarray(X1, np.float32)
+    X2 = np.ascontiguousarray(X2, np.float32)
+    R, K1 = X1.shape
+    K2 = X2.shape[1]
+    Cm = np.empty((K1, K2), np.float32)
+    _check(lib.mc_panel_gram(R, K1, K2, X1.ctypes.data_as(C.c_void_p), X2.ctypes.data_as(C.c_void_p),
+                             Cm.ctypes.data_as(C.c_void_p), 1 if tensor_cores else 0), "mc_panel_gram")
+    return Cm
+
+
 def orth_block(X, Qp=None, stream=None):
     """Orthonormal basis of (I - Qp Qp^T) X for CUDA float32 tensors X (R x K)
     and Qp (R x cols), K and cols multiples of 4 (mc_orth_block).  X is

@@ -87,6 +87,7 @@ _SIGS = {
     "mc_gram_tc": (C.c_int, [C.c_int64, C.c_int, _P, _P]),
     "mc_panel_gemm": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "mc_gather_rate": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "mc_panel_gram": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "mc_gram_noalloc": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int, _P, C.c_int, _P]),
     "mc_server_create": (C.c_int, [C.POINTER(_P), C.c_size_t, C.c_int, C.c_int, C.c_int]),
     "mc_server_destroy": (None, [_P]),

@@ -1141,8 +1141,28 @@ static TnPlan tn_plan(int64_t R, int K1, int K2, bool sym) {
 
 size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2) {
   // the largest plan over sym / non-sym (sym has fewer active tiles, more splits)
+  // and over the tensor-core kernel
   const TnPlan a = tn_plan(R, K1, K2, true), b = tn_plan(R, K1, K2, false);
-  return std::max((size_t)a.nsplit * a.K1p * a.K2p, (size_t)b.nsplit * b.K1p * b.K2p);
+  size_t n = std::max((size_t)a.nsplit * a.K1p * a.K2p, (size_t)b.nsplit * b.K1p * b.K2p);
+  if (K1 <= 256 && K2 <= 256) n = std::max(n, gemm_tn_tc_scratch_floats(R, K1, K2));
+  return n;
+}
+
+// MC_TN_TC=0 keeps the SIMT kernels for X1^T X2.
+bool use_tn_tc() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_TN_TC");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+void gemm_tn_reduce_partials(cudaStream_t st, int K1, int K2, int nsplit, const float *partial, int K1p, int K2p,
+                             float *C, int ld_c, const int *skip) {
+  const int64_t total = (int64_t)K1 * K2;
+  const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
+  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, nsplit, partial, K1p, K2p, false, 4, C, ld_c, skip);
+  MC_CHECK_LAUNCH();
 }
 
 template <int T>
@@ -1160,7 +1180,17 @@ static void launch_tn_small(cudaStream_t st, int64_t R, int K1, int K2, const fl
 }
 
 void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y, int ld_y, float *C,
-             int ld_c, bool sym, float *partial, const int *skip) {
+             int ld_c, bool sym, float *partial, const int *skip, int *err) {
+  if (K1 <= 0 || K2 <= 0) return;
+  if (use_tn_tc() && K2 > 16 && gemm_tn_tc_supported(R, K1, K2, X, ld_x, Y, ld_y)) {
+    gemm_tn_tc(st, R, K1, K2, X, ld_x, Y, ld_y, C, ld_c, partial, err, skip);
+    return;
+  }
+  gemm_tn_simt(st, R, K1, K2, X, ld_x, Y, ld_y, C, ld_c, partial, skip, sym);
+}
+
+void gemm_tn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y, int ld_y,
+                  float *C, int ld_c, float *partial, const int *skip, bool sym) {
   if (K1 <= 0 || K2 <= 0) return;
   MC_REQUIRE(ld_x % 4 == 0 && ld_y % 4 == 0, "gemm_tn: leading dims must be multiples of 4");
   MC_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0,

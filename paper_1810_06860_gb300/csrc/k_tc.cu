@@ -593,6 +593,215 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
   if (tid == 0 && s_fail && err) atomicOr(err, s_fail << 8);
 }
 
+// ---- X1^T X2 on the tensor cores (Grams and projections) --------------------
+// C (K1 x K2) = X1^T X2 summed over R rows, X1 (R x K1) and X2 (R x K2) tall
+// float32 panels, K1, K2 <= 256: the Grams of the block orthonormalisation
+// (Alg. 5 steps 3-7 as CholeskyQR, Lemmas 2-3), its projections Q_prev^T X
+// and the Ritz Gram B B^T (Alg. 5 step 9, Alg. 3 step 1).  The MMA's
+// reduction dimension is the panels' rows, so every 32-row stage is
+// transposed into the K-major operand layout (as in gram_tc_kernel).  Each
+// CTA covers a range of rows and writes one partial K1_p x K2_p tile; a
+// fixed-order reduction adds the partials.
+//
+// Warp-specialised, 384 threads:
+//   warp 0, lane 0   TMA producer: the stage's 32-column boxes of X1 (and of
+//                    X2 unless it is X1) once the splitters released the stage;
+//   warps 4..11      split every value into TF32 hi and lo (rounded to nearest)
+//                    and write both transposed, then release the raw stage
+//                    and hand the split stage to the issuer;
+//   warp 1, lane 0   MMA issuer: hi*hi + hi*lo + lo*hi for every 8-row step
+//                    into one accumulator per 128 columns of X1, releasing the
+//                    split stage by a commit;
+//   warps 8..11      after the last stage, read the accumulators (tcgen05.ld)
+//                    and write the partial tile.
+// Every wait is bounded; an expiry ends every role, each drains its own
+// copies or MMAs, and the error code goes to err.
+constexpr int TT_THREADS = 384, TT_KT = 32, TT_MAXST = 6;
+constexpr int TT_BOX = TT_KT * 32 * 4;  // 32 rows x 32 columns: 4 KiB
+
+__global__ void __launch_bounds__(TT_THREADS, 1)
+gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, int same,
+                     int64_t R, int nbA, int nbB, int Np, int mt, uint32_t tmem_cols, int nst, int64_t rows_per_cta,
+                     float *__restrict__ partial, int K1p, int K2p, int *__restrict__ err,
+                     const int *__restrict__ skip) {
+  extern __shared__ __align__(1024) uint8_t tt_raw_smem[];
+  __shared__ __align__(8) uint64_t full_bar[TT_MAXST], rawfree_bar[TT_MAXST], split_bar[TT_MAXST],
+      splitfree_bar[TT_MAXST];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int s_fail;
+  if (skip && *skip) return;  // a pass the previous one made unnecessary
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tt_raw_smem) + 1023) & ~uintptr_t(1023));
+  const int nbr = nbA + (same ? 0 : nbB);                  // raw boxes per stage
+  const size_t raw_bytes = (size_t)nbr * TT_BOX;
+  const size_t spl_bytes = (size_t)(4 * mt + (same ? 0 : nbB)) * TT_BOX;  // one of hi / lo
+  const size_t stage_bytes = raw_bytes + 2 * spl_bytes;
+  auto raw = [&](int s) { return base + (size_t)s * stage_bytes; };
+  auto hi = [&](int s) { return base + (size_t)s * stage_bytes + raw_bytes; };
+  auto lo = [&](int s) { return base + (size_t)s * stage_bytes + raw_bytes + spl_bytes; };
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int64_t r0 = blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(R, r0 + rows_per_cta);
+  const int S = r1 > r0 ? static_cast<int>((r1 - r0 + TT_KT - 1) / TT_KT) : 0;
+  volatile int *vfail = &s_fail;
+  const unsigned fullm = 0xffffffffu;
+
+  if (tid == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&rawfree_bar[s], 8);  // one arrival per split warp
+      mbar_init(&split_bar[s], 8);
+      mbar_init(&splitfree_bar[s], 1);  // MMA commit
+    }
+    mbar_init(&acc_bar, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  // A (X1^T) is laid out as 4 mt boxes (128 columns per accumulator: the MMA
+  // reads 128 rows of A whatever K1), B (X2^T) follows unless it is A
+  const int aboxes = 4 * mt;
+  if (wid == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      int issued = 0;
+      for (int g = 0; g < S; ++g) {
+        if (failed(vfail)) break;
+        const int s = g % nst;
+        if (g >= nst && !mbar_wait(&rawfree_bar[s], ((g / nst) - 1) & 1)) {
+          atomicOr(&s_fail, 1);
+          break;
+        }
+        mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(raw_bytes));
+        const int y = static_cast<int>(r0 + (int64_t)g * TT_KT);
+        for (int j = 0; j < nbA; ++j) tma_load_2d(raw(s) + j * TT_BOX, &amap, 32 * j, y, &full_bar[s]);
+        if (!same)
+          for (int j = 0; j < nbB; ++j) tma_load_2d(raw(s) + (nbA + j) * TT_BOX, &bmap, 32 * j, y, &full_bar[s]);
+        issued = g + 1;
+      }
+      for (int g = max(0, issued - nst); g < issued; ++g) mbar_wait(&full_bar[g % nst], (g / nst) & 1);
+    }
+  } else if (wid == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, Np);
+      int committed = -1;
+      for (int g = 0; g < S; ++g) {
+        if (failed(vfail)) break;
+        const int s = g % nst;
+        if (!mbar_wait(&split_bar[s], (g / nst) & 1)) {
+          atomicOr(&s_fail, 4);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ah = smem_u32(hi(s)), al = smem_u32(lo(s));
+        const uint32_t bh = same ? ah : ah + aboxes * TT_BOX, bl = same ? al : al + aboxes * TT_BOX;
+#pragma unroll
+        for (int ks = 0; ks < TT_KT / 8; ++ks) {
+          const uint32_t ko = ks * 32;
+          const uint32_t acc0 = (g > 0 || ks > 0) ? 1u : 0u;
+          for (int t = 0; t < mt; ++t) {
+            const uint32_t d = tmem + static_cast<uint32_t>(t * Np);
+            const uint32_t ao = static_cast<uint32_t>(t) * 16 * 1024 + ko;  // 128 columns = 16 atoms further
+            mma_tf32(d, smem_desc(ah + ao), smem_desc(bh + ko), idesc, acc0);
+            mma_tf32(d, smem_desc(ah + ao), smem_desc(bl + ko), idesc, 1u);
+            mma_tf32(d, smem_desc(al + ao), smem_desc(bh + ko), idesc, 1u);
+          }
+        }
+        mma_commit(&splitfree_bar[s]);
+        committed = g;
+      }
+      if (S > 0 && committed == S - 1) mma_commit(&acc_bar);
+      if (committed >= 0 && !mbar_wait(&splitfree_bar[committed % nst], (committed / nst) & 1)) atomicOr(&s_fail, 8);
+    }
+  } else if (wid >= 4) {
+    // ---- transpose and split ----
+    const int st = tid - 128;
+    for (int g = 0; g < S; ++g) {
+      if (__any_sync(fullm, failed(vfail))) break;
+      const int s = g % nst;
+      bool ok = mbar_wait(&full_bar[s], (g / nst) & 1);
+      if (ok && g >= nst) ok = mbar_wait(&splitfree_bar[s], ((g / nst) - 1) & 1);
+      if (!__all_sync(fullm, ok)) {
+        atomicOr(&s_fail, 2);
+        break;
+      }
+      // TMA box j holds element (row r, column 32 j + cc) at
+      //   j * 1024 + r * 32 + (((cc / 4) ^ (r % 8)) * 4) + cc % 4   (floats);
+      // the K-major operand stores global column c at
+      //   (c / 8) * 256 + (c % 8) * 32 + (((r / 4) ^ (c % 8)) * 4) + r % 4,
+      // with B's columns after A's 4 mt boxes.  A warp takes one 4-column
+      // group of a box across its 32 rows (lane = row): conflict-free.
+      const float4 *src = reinterpret_cast<const float4 *>(raw(s));
+      float *dh = reinterpret_cast<float *>(hi(s)), *dl = reinterpret_cast<float *>(lo(s));
+      for (int q = st; q < nbr * 256; q += 256) {
+        const int box = q >> 8, k4 = (q >> 5) & 7, r = q & 31;
+        const int obox = box < nbA ? box : aboxes + (box - nbA);
+        const int c0 = obox * 32 + k4 * 4;
+        const float4 v = src[box * 256 + r * 8 + (k4 ^ (r & 7))];
+        const float vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + u;
+          const int off = (c >> 3) * 256 + (c & 7) * 32 + ((((r >> 2) ^ (c & 7)) & 7) << 2) + (r & 3);
+          float h, l;
+          tf32_split(vals[u], h, l);
+          dh[off] = h;
+          dl[off] = l;
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&rawfree_bar[s]);
+        mbar_arrive(&split_bar[s]);
+      }
+    }
+  }
+  __syncthreads();
+  if (wid >= 8) {
+    // ---- partial tile: accumulator t holds rows 128 t .. of C, lane = row ----
+    const int ew = wid - 8;
+    bool ok = !__any_sync(fullm, failed(vfail)) && S > 0;
+    if (ok) {
+      const bool w = mbar_wait(&acc_bar, 0);
+      if (!__all_sync(fullm, w)) {
+        atomicOr(&s_fail, 16);
+        ok = false;
+      }
+    }
+    tc_fence_after();
+    float *out = partial + (size_t)blockIdx.x * K1p * K2p;
+    for (int t = 0; t < mt; ++t) {
+      const int i = t * 128 + 32 * ew + lane;
+      for (int c0 = 0; c0 < Np; c0 += 16) {
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+        if (ok) tmem_ld16(tmem + (static_cast<uint32_t>(32 * ew) << 16) + static_cast<uint32_t>(t * Np + c0), v);
+        if (i < K1p) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (c0 + k < K2p) out[(size_t)i * K2p + c0 + k] = v[k];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  if (tid == 0 && s_fail && err) atomicOr(err, s_fail << 16);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::mutex mu;
@@ -672,6 +881,75 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
   gemm_nn_tc_ws_kernel<<<grid, NW_THREADS, p.smem, st>>>(map, R, K, N, p.Kp, p.Np, p.cols, p.nst, W, ld_w, colscale,
                                                           alpha, beta, Z, ld_z, err, copy_if, ld_x, X);
   MC_CHECK_LAUNCH();
+}
+
+// ---- X1^T X2 (tensor cores) ----------------------------------------------------
+namespace {
+constexpr size_t TT_SMEM = 226 * 1024;
+struct TtPlan {
+  int K1p, K2p, nbA, nbB, Np, mt, nst, nsplit;
+  uint32_t cols;
+  size_t smem;
+  int64_t rows_per;
+};
+TtPlan tt_plan(int64_t R, int K1, int K2, bool same) {
+  TtPlan p{};
+  p.K1p = static_cast<int>(round_up(K1, 32));
+  p.K2p = static_cast<int>(round_up(K2, 32));
+  p.nbA = p.K1p / 32;
+  p.nbB = same ? 0 : p.K2p / 32;
+  p.Np = static_cast<int>(round_up(K2, 16));
+  p.mt = p.K1p > 128 ? 2 : 1;
+  const size_t raw = (size_t)(p.nbA + p.nbB) * TT_BOX, spl = (size_t)(4 * p.mt + p.nbB) * TT_BOX;
+  const size_t stage = raw + 2 * spl;
+  p.nst = static_cast<int>(std::min<size_t>(TT_MAXST, (TT_SMEM - 1024) / stage));
+  p.smem = (size_t)p.nst * stage + 1024;
+  p.cols = 32;
+  while (p.cols < static_cast<uint32_t>(p.mt * p.Np)) p.cols <<= 1;
+  p.nsplit = tc_nsplit(R);
+  p.rows_per = round_up((R + p.nsplit - 1) / p.nsplit, TT_KT);
+  p.nsplit = static_cast<int>((R + p.rows_per - 1) / p.rows_per);
+  return p;
+}
+CUtensorMap tt_map(const float *X, int64_t R, int K, int ld) {
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(R)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  const cuuint32_t box[2] = {32, static_cast<cuuint32_t>(TT_KT)};
+  const cuuint32_t estride[2] = {1, 1};
+  const CUresult cr = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), gdim, gstride, box,
+                                  estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) fail(MC_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)cr));
+  return map;
+}
+}  // namespace
+
+bool gemm_tn_tc_supported(int64_t R, int K1, int K2, const void *X1, int ld1, const void *X2, int ld2) {
+  if (R < 1 || R >= (int64_t(1) << 31) || K1 < 1 || K2 < 1 || K1 > 256 || K2 > 256) return false;
+  if (ld1 < K1 || ld2 < K2 || ld1 % 4 || ld2 % 4) return false;
+  if (((reinterpret_cast<uintptr_t>(X1) | reinterpret_cast<uintptr_t>(X2)) & 15u) != 0) return false;
+  return tt_plan(R, K1, K2, X1 == X2 && ld1 == ld2 && K1 == K2).nst >= 2;
+}
+
+size_t gemm_tn_tc_scratch_floats(int64_t R, int K1, int K2) {
+  const TtPlan p = tt_plan(R, K1, K2, false);
+  return (size_t)p.nsplit * p.K1p * p.K2p;
+}
+
+void gemm_tn_tc(cudaStream_t st, int64_t R, int K1, int K2, const float *X1, int ld1, const float *X2, int ld2,
+                float *C, int ld_c, float *partial, int *err, const int *skip) {
+  MC_REQUIRE(gemm_tn_tc_supported(R, K1, K2, X1, ld1, X2, ld2), "gemm_tn_tc: shape or alignment not supported");
+  const bool same = X1 == X2 && ld1 == ld2 && K1 == K2;
+  const TtPlan p = tt_plan(R, K1, K2, same);
+  const CUtensorMap amap = tt_map(X1, R, K1, ld1);
+  const CUtensorMap bmap = same ? amap : tt_map(X2, R, K2, ld2);
+  MC_CUDA(cudaFuncSetAttribute(gemm_tn_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM));
+  gemm_tn_tc_ws_kernel<<<p.nsplit, TT_THREADS, p.smem, st>>>(amap, bmap, same ? 1 : 0, R, p.nbA, p.nbB, p.Np, p.mt,
+                                                              p.cols, p.nst, p.rows_per, partial, p.K1p, p.K2p,
+                                                              err, skip);
+  MC_CHECK_LAUNCH();
+  gemm_tn_reduce_partials(st, K1, K2, p.nsplit, partial, p.K1p, p.K2p, C, ld_c, skip);
 }
 
 size_t gram_tc_scratch_floats(int64_t R, int K) {

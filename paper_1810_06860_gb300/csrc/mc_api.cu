@@ -455,6 +455,17 @@ void spmm_Yt(mc_handle h, const float *X, int ld_x, int K, float *out, int ld_ou
 // wait expires (checked after every Ritz eigensolve).
 int *tc_err(mc_handle h) { return h->flags.p ? h->flags.as<int>() + 3 : nullptr; }
 
+// The warp-specialised tensor-core X1^T X2 (through gemm_tn) takes this Gram
+// (MC_TN_TC=0 and MC_GRAM_WS=0 keep the older tensor-core Gram above 64 columns).
+bool tn_tc_covers(int64_t R, int K, const float *X, int ld) {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_GRAM_WS");
+    return !(v && v[0] == '0');
+  }();
+  const char *t = std::getenv("MC_TN_TC");
+  return on && !(t && t[0] == '0') && K > 16 && gemm_tn_tc_supported(R, K, K, X, ld, X, ld);
+}
+
 // Gram X^T X: the tensor-core kernel (tcgen05, 3xTF32) for tc_min_k() <= K
 // <= 256, SIMT otherwise; MC_GRAM_SIMT=1 selects SIMT everywhere.
 bool use_tensor_gram() {
@@ -475,13 +486,13 @@ int tc_min_k() {
 
 void gram(mc_handle h, int64_t R, int K, const float *X, int ld, float *Gout, int ldg, const int *skip = nullptr) {
   Scope sc(h, MC_T_GRAM, 4.0 * R * K + 4.0 * K * K, 1.0 * R * K * (K + 1));
-  if (!skip && use_tensor_gram() && K >= tc_min_k() && gram_tc_supported(K, ld, X)) {
+  if (!skip && use_tensor_gram() && K >= tc_min_k() && gram_tc_supported(K, ld, X) && !tn_tc_covers(R, K, X, ld)) {
     fbuf(h, h->tn_part, gram_tc_scratch_floats(R, K));
     gram_tc(h->stream, R, K, X, ld, Gout, ldg, h->tn_part.as<float>(), h->flags.as<int>() + 3);
     return;
   }
   fbuf(h, h->tn_part, gemm_tn_scratch_floats(R, K, K));
-  gemm_tn(h->stream, R, K, K, X, ld, X, ld, Gout, ldg, true, h->tn_part.as<float>(), skip);
+  gemm_tn(h->stream, R, K, K, X, ld, X, ld, Gout, ldg, true, h->tn_part.as<float>(), skip, tc_err(h));
 }
 
 // One CholeskyQR pass: out = X R^{-1} with X^T X + shift I = R^T R.
@@ -528,7 +539,7 @@ void project_out(mc_handle h, int64_t R, const float *Qp, int ldq, int cols, flo
   for (int rep = 0; rep < 2; ++rep) {
     {
       Scope sc(h, MC_T_GRAM, 4.0 * R * (cols + K), 2.0 * R * cols * K);
-      gemm_tn(h->stream, R, cols, K, Qp, ldq, X, ldx, C, K, false, h->tn_part.as<float>());
+      gemm_tn(h->stream, R, cols, K, Qp, ldq, X, ldx, C, K, false, h->tn_part.as<float>(), nullptr, tc_err(h));
     }
     Scope sc(h, MC_T_GEMM, 4.0 * R * (cols + 2 * K), 2.0 * R * cols * K);
     gemm_nn(h->stream, R, cols, K, Qp, ldq, C, K, nullptr, -1.0f, 1.0f, X, ldx, nullptr, tc_err(h));
@@ -1367,6 +1378,42 @@ mc_status mc_svt_sample(mc_handle h, int64_t count, const int64_t *rows, const i
     dc.release(h->alloc);
     dout.release(h->alloc);
     sync(h);
+    return MC_OK;
+  });
+}
+
+mc_status mc_panel_gram(int64_t R, int K1, int K2, const float *X1, const float *X2, float *C, int tensor_cores) {
+  if (R < 1 || K1 < 1 || K2 < 1 || !X1 || !X2 || !C) return MC_EINVAL;
+  const int k1p = (int)round_up(K1, 4), k2p = (int)round_up(K2, 4);
+  const bool same = X1 == X2 && K1 == K2;  // a Gram: one staged panel serves both operands
+  if (tensor_cores && !gemm_tn_tc_supported(R, K1, K2, reinterpret_cast<const void *>(256), k1p,
+                                            reinterpret_cast<const void *>(same ? 256 : 512), k2p))
+    return MC_EINVAL;
+  return guarded([&]() -> mc_status {
+    DBuf d1, d2, dc, dp, de;
+    Alloc a;
+    BufGuard g(a, {&d1, &d2, &dc, &dp, &de});
+    d1.reserve(a, sizeof(float) * R * k1p);
+    d2.reserve(a, sizeof(float) * R * k2p);
+    dc.reserve(a, sizeof(float) * K1 * K2);
+    dp.reserve(a, sizeof(float) * gemm_tn_scratch_floats(R, K1, K2));
+    de.reserve(a, sizeof(int));
+    MC_CUDA(cudaMemset(de.p, 0, sizeof(int)));
+    MC_CUDA(cudaMemset(d1.p, 0, sizeof(float) * R * k1p));
+    MC_CUDA(cudaMemset(d2.p, 0, sizeof(float) * R * k2p));
+    MC_CUDA(cudaMemcpy2D(d1.p, sizeof(float) * k1p, X1, sizeof(float) * K1, sizeof(float) * K1, R, cudaMemcpyDefault));
+    MC_CUDA(cudaMemcpy2D(d2.p, sizeof(float) * k2p, X2, sizeof(float) * K2, sizeof(float) * K2, R, cudaMemcpyDefault));
+    const float *x2 = same ? d1.as<float>() : d2.as<float>();
+    if (tensor_cores)
+      gemm_tn_tc(0, R, K1, K2, d1.as<float>(), k1p, x2, k2p, dc.as<float>(), K2, dp.as<float>(), de.as<int>(),
+                 nullptr);
+    else
+      gemm_tn_simt(0, R, K1, K2, d1.as<float>(), k1p, x2, k2p, dc.as<float>(), K2, dp.as<float>(), nullptr, same);
+    int herr = 0;
+    MC_CUDA(cudaMemcpy(&herr, de.p, sizeof(int), cudaMemcpyDeviceToHost));
+    MC_CUDA(cudaMemcpy(C, dc.p, sizeof(float) * K1 * K2, cudaMemcpyDefault));
+    MC_CUDA(cudaDeviceSynchronize());
+    if (herr) fail(MC_ETIMEOUT, "a bounded wait in the tensor-core panel Gram expired");
     return MC_OK;
   });
 }

@@ -183,8 +183,23 @@ void sample_lowrank(cudaStream_t st, int64_t count, const int64_t *rows, const i
 size_t gemm_tn_scratch_floats(int64_t R, int K1, int K2);
 // skip (device int, may be NULL): when it holds a nonzero value the kernels
 // return without work (a CholeskyQR pass found unnecessary on the device).
+// Shapes the tensor-core kernel takes (K1, K2 <= 256, K2 > 16) run there
+// unless MC_TN_TC=0; err (device int, may be NULL) receives its wait-expiry code.
 void gemm_tn(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y,
-             int ld_y, float *C, int ld_c, bool sym, float *partial, const int *skip = nullptr);
+             int ld_y, float *C, int ld_c, bool sym, float *partial, const int *skip = nullptr,
+             int *err = nullptr);
+// The SIMT kernels alone.
+void gemm_tn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, int ld_x, const float *Y, int ld_y,
+                  float *C, int ld_c, float *partial, const int *skip = nullptr, bool sym = false);
+// The fixed-order sum of nsplit partial K1p x K2p tiles into C (K1 x K2).
+void gemm_tn_reduce_partials(cudaStream_t st, int K1, int K2, int nsplit, const float *partial, int K1p, int K2p,
+                             float *C, int ld_c, const int *skip);
+// C (K1 x K2) = X1^T X2 on the tensor cores (k_tc.cu, 3xTF32, warp-specialised):
+// K1, K2 <= 256, leading dimensions multiples of 4, panels 16-byte aligned.
+bool gemm_tn_tc_supported(int64_t R, int K1, int K2, const void *X1, int ld1, const void *X2, int ld2);
+size_t gemm_tn_tc_scratch_floats(int64_t R, int K1, int K2);
+void gemm_tn_tc(cudaStream_t st, int64_t R, int K1, int K2, const float *X1, int ld1, const float *X2, int ld2,
+                float *C, int ld_c, float *partial, int *err, const int *skip);
 // Z (R x K2, ld_z) = beta * Z + alpha * X (R x K1, ld_x) * W (K1 x K2, ld_w) * diag(colscale)
 // colscale may be NULL (ones).  Z may not alias X.  copy_if (device int, may
 // be NULL; 16 < K1 == K2 <= 64 only): when it holds a nonzero value, Z = X.

@@ -275,3 +275,33 @@ def test_gather_rate_probe(mc):
             assert np.isfinite(g) and g > 0
         with pytest.raises(mc.McError):
             h.gather_rate(256)
+
+
+@pytest.mark.parametrize("R,K1,K2,same", [(138_000, 60, 60, True), (138_000, 180, 60, False), (27_000, 240, 240, True),
+                                          (1_000, 17, 33, False), (300, 256, 32, False), (129, 64, 20, False)])
+def test_panel_gram_tensor_cores(mc, R, K1, K2, same):
+    """C = X1^T X2 on the tensor cores (3xTF32) against float64 and against the
+    SIMT kernels: every entry within 1e-5 of max |X1|^T |X2|, scaled by
+    sqrt(R / 1000) for the float32 sums over R rows (the Gram tests' bound);
+    ragged R (not a multiple of the 32-row stage), K1 and K2 (not multiples of
+    the 32-column box) are covered."""
+    rng = np.random.default_rng(R + K1 + K2)
+    X1 = rng.standard_normal((R, K1)).astype(np.float32)
+    X2 = X1 if same else rng.standard_normal((R, K2)).astype(np.float32)
+    Ct = mc.panel_gram(X1, X2, tensor_cores=True)
+    ref = X1.astype(np.float64).T @ X2.astype(np.float64)
+    bound = (np.abs(X1).astype(np.float64).T @ np.abs(X2).astype(np.float64)).max()
+    tol = 1e-5 * bound * max(1.0, np.sqrt(R / 1000))
+    assert np.max(np.abs(Ct - ref)) <= tol
+    Cs = mc.panel_gram(X1, X2, tensor_cores=False)
+    assert np.max(np.abs(Ct - Cs)) <= 2 * tol
+
+
+def test_panel_gram_tensor_cores_rejects_two_wide_panels(mc):
+    """Two different 256-column panels need more shared memory per stage than
+    the kernel's two-stage minimum: rejected with nothing run (the library's
+    products fall back to SIMT for them)."""
+    X = np.zeros((10, 256), np.float32)
+    Y = np.zeros((10, 256), np.float32)
+    with pytest.raises(mc.McError):
+        mc.panel_gram(X, Y, tensor_cores=True)
