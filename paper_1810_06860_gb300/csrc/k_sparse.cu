@@ -724,8 +724,6 @@ void plan_segments(cudaStream_t st, Alloc &a, int64_t rows, const int *ptr, SegP
   MC_CUDA(cudaStreamSynchronize(st));
 }
 
-namespace {
-int lane_groups(int K4) { return K4 <= 2 ? 16 : (K4 <= 4 ? 8 : (K4 <= 8 ? 4 : (K4 <= 16 ? 2 : 1))); }
 int default_chunk(int64_t rows_in) {
   // column chunks of at most 128, narrower when the panel slice would not stay
   // resident in L2 next to the streamed indices (each chunk re-reads them)
@@ -733,6 +731,9 @@ int default_chunk(int64_t rows_in) {
   while (chunk > 32 && (double)rows_in * chunk * 4.0 > 40e6) chunk /= 2;
   return chunk;
 }
+
+namespace {
+int lane_groups(int K4) { return K4 <= 2 ? 16 : (K4 <= 4 ? 8 : (K4 <= 8 ? 4 : (K4 <= 16 ? 2 : 1))); }
 
 template <int G>
 void launch_seg(int u, int64_t blocks, int threads, cudaStream_t st, int64_t nseg, const int4 *segs, const int *idx,

@@ -319,10 +319,16 @@ double spmm_bytes(int64_t nnz, int64_t rows, int64_t rows_in, int K) {
 // of the process.  The candidates differ only in launch shape, never in the
 // order of any sum, so tuning cannot change a result.  MC_SPMM_TUNE=0 keeps
 // the default shape; MC_SPMM_TUNE_LOG=1 prints the measurements to stderr.
+// A shape class: direction, what the candidate launch shapes depend on (lane
+// groups, default chunk, whether a half chunk is offered) and log2 of the
+// rows, input rows and entries.  Panel widths with the same candidates share
+// a class, so a served job whose k grows by a few columns, or a new job of a
+// similar size, reuses the measured shape instead of timing the candidates
+// again.
 struct TuneKey {
-  int trans, K, lr, lri, lnnz;
+  int trans, G, dc, wide, lr, lri, lnnz;
   bool operator<(const TuneKey &o) const {
-    return std::tie(trans, K, lr, lri, lnnz) < std::tie(o.trans, o.K, o.lr, o.lri, o.lnnz);
+    return std::tie(trans, G, dc, wide, lr, lri, lnnz) < std::tie(o.trans, o.G, o.dc, o.wide, o.lr, o.lri, o.lnnz);
   }
 };
 std::mutex g_tune_mu;
@@ -364,7 +370,8 @@ template <class F>
 SpmmCfg tuned_cfg(mc_handle h, int trans, int K, int64_t rows, int64_t rows_in, F &&launch) {
   if (const SpmmCfg *f = forced_cfg()) return *f;
   if (!tune_enabled()) return SpmmCfg{};
-  const TuneKey key{trans, K, ilog2(rows), ilog2(rows_in), ilog2(std::max<int64_t>(h->nnz, 1))};
+  const TuneKey key{trans, spmm_groups(K, rows_in), default_chunk(rows_in), K > 32 ? 1 : 0, ilog2(rows),
+                    ilog2(rows_in), ilog2(std::max<int64_t>(h->nnz, 1))};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);

@@ -139,6 +139,10 @@ struct SpmmCfg {
   int u = 0, threads = 0, chunk = 0;
 };
 std::vector<SpmmCfg> spmm_candidates(int K, int64_t rows_in);
+// What the candidate list depends on: lane groups per warp and the default
+// column chunk for a panel of K columns and rows_in rows.
+int spmm_groups(int K, int64_t rows_in);
+int default_chunk(int64_t rows_in);
 void spmm(cudaStream_t st, const SegPlan &plan, const int *idx, const float *val, int64_t rows_in,
           const float *X, int ld_x, int K, float *out, int ld_out, float *partial, const SpmmCfg &cfg = SpmmCfg{});
 // As spmm with a bf16 panel X (K, ld_x multiples of 8, K <= 256), float32
