@@ -347,16 +347,16 @@ constexpr int NT_BOX_BYTES = NT_BM * NT_KC * 4;  // 16 KiB
 constexpr int NT_MAX_W = 16384;                   // K_p * N_p floats
 constexpr size_t NT_SMEM_LIMIT = 220 * 1024;
 
-// The kernel is warp-specialised: 384 threads in roles that hand boxes to each other through mbarriers:
+// The kernel is warp-specialised: 512 threads in roles that hand boxes to each other through mbarriers:
 //   warp 0, lane 0   TMA producer: loads box g into stage g % nst once the
 //                    MMAs of box g - nst released it;
 //   warp 1, lane 0   MMA issuer: hi*hi + hi*lo + lo*hi per 8-column step into
 //                    one of two TMEM accumulators (tiles alternate), releases
 //                    the stage (commit) and, after a tile's last box, hands
 //                    the accumulator to the epilogue (commit);
-//   warps 4..7       split each landed box in place into TF32 hi and float32
-//                    lo and signal the issuer;
-//   warps 8..11      epilogue: each reads its 32 accumulator rows (tcgen05.ld,
+//   warps 4..11      split each landed box in place into TF32 hi and lo and
+//                    signal the issuer;
+//   warps 12..15     epilogue: each reads its 32 accumulator rows (tcgen05.ld,
 //                    lanes 32 (w % 4) ..), stages 32 columns at a time in its
 //                    own shared memory and writes whole rows with float4
 //                    stores, then frees the accumulator.
@@ -365,7 +365,7 @@ constexpr size_t NT_SMEM_LIMIT = 220 * 1024;
 // a shared failure flag that ends every role's loop; each role then waits
 // (bounded) for its own outstanding copies or MMAs before the block frees its
 // tensor memory.
-constexpr int NW_THREADS = 384;
+constexpr int NW_THREADS = 512;
 constexpr int NW_MAXST = 4;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -408,7 +408,7 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
   if (tid == 0) {
     for (int s = 0; s < nst; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&split_bar[s], 4);   // one arrival per split warp
+      mbar_init(&split_bar[s], 8);   // one arrival per split warp
       mbar_init(&empty_bar[s], 1);   // MMA commit
     }
     for (int a = 0; a < 2; ++a) {
@@ -503,7 +503,7 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
       // the last commit covers every MMA issued before it
       if (committed >= 0 && !mbar_wait(&empty_bar[committed % nst], (committed / nst) & 1)) atomicOr(&s_fail, 64);
     }
-  } else if (wid >= 4 && wid < 8) {
+  } else if (wid >= 4 && wid < 12) {
     // ---- split into TF32 hi (in place) and float32 lo ----
     const int st = tid - 128;
     for (int g = 0; g < G; ++g) {
@@ -517,7 +517,7 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
       float4 *hi4 = reinterpret_cast<float4 *>(box_hi(s));
       float4 *lo4 = reinterpret_cast<float4 *>(box_lo(s));
 #pragma unroll 4
-      for (int q = st; q < NT_BOX_BYTES / 16; q += 128) {
+      for (int q = st; q < NT_BOX_BYTES / 16; q += 256) {
         const float4 v = hi4[q];
         float4 h, l;
         tf32_split(v.x, h.x, l.x);
@@ -531,9 +531,9 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
       __syncwarp();
       if (lane == 0) mbar_arrive(&split_bar[s]);
     }
-  } else if (wid >= 8) {
+  } else if (wid >= 12) {
     // ---- epilogue: accumulator rows 32 (w % 4) .. + 31 of each tile ----
-    const int ew = wid - 8;
+    const int ew = wid - 12;
     float4 *buf4 = reinterpret_cast<float4 *>(epi) + ew * 32 * 8;  // 32 rows x 8 float4
     const bool vec_out = ld_z % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15u) == 0;
     for (int tl = 0; tl < my_tiles; ++tl) {
