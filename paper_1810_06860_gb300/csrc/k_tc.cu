@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 namespace mc {
@@ -74,6 +75,30 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bulk tensor stores from shared memory (plain, or added to what global
+// memory holds), grouped for completion by the issuing thread.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void tma_add_2d(const CUtensorMap *map, const void *src, int x, int y) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int P>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(P) : "memory");
+}
+template <int P>
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group %0;" ::"n"(P) : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -345,11 +370,12 @@ gram_tc_reduce_kernel(int K, int nsplit, const float *__restrict__ partial, int 
 constexpr int NT_BM = 128, NT_KC = 32;
 constexpr int NT_BOX_BYTES = NT_BM * NT_KC * 4;  // 16 KiB
 constexpr int NT_MAX_W = 16384;                   // K_p * N_p floats
-constexpr size_t NT_SMEM_LIMIT = 220 * 1024;
+constexpr size_t NT_SMEM_LIMIT = 226 * 1024;
 
 // The kernel is warp-specialised: 512 threads in roles that hand boxes to each other through mbarriers:
 //   warp 0, lane 0   TMA producer: loads box g into stage g % nst once the
-//                    MMAs of box g - nst released it;
+//                    MMAs of box g - nst released it (the first nst boxes
+//                    before W is staged);
 //   warp 1, lane 0   MMA issuer: hi*hi + hi*lo + lo*hi per 8-column step into
 //                    one of two TMEM accumulators (tiles alternate), releases
 //                    the stage (commit) and, after a tile's last box, hands
@@ -357,9 +383,13 @@ constexpr size_t NT_SMEM_LIMIT = 220 * 1024;
 //   warps 4..11      split each landed box in place into TF32 hi and lo and
 //                    signal the issuer;
 //   warps 12..15     epilogue: each reads its 32 accumulator rows (tcgen05.ld,
-//                    lanes 32 (w % 4) ..), stages 32 columns at a time in its
-//                    own shared memory and writes whole rows with float4
-//                    stores, then frees the accumulator.
+//                    lanes 32 (w % 4) ..), scales them and stages 32 columns
+//                    at a time in its own shared memory (one or two
+//                    buffers), from where one lane hands them to a bulk
+//                    tensor store (beta = 0) or a bulk tensor add into Z
+//                    (beta = 1), then frees the accumulator.  Other beta
+//                    values, or a Z the tensor map cannot describe, take
+//                    float4 stores from the staging buffer instead.
 // So the split of box g + 1, the MMAs of box g and the epilogue of the
 // previous tile run at the same time.  Every wait is bounded: an expiry sets
 // a shared failure flag that ends every role's loop; each role then waits
@@ -375,7 +405,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 __device__ __forceinline__ bool failed(const volatile int *f) { return *f != 0; }
 
 __global__ void __launch_bounds__(NW_THREADS, 1)
-gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int N, int Kp, int Np,
+gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap zmap, int zmode,
+                     int ebuf, int64_t R, int K, int N, int Kp, int Np,
                      uint32_t tmem_cols, int nst, const float *__restrict__ W, int ld_w,
                      const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z, int ld_z,
                      int *__restrict__ err, const int *__restrict__ copy_if, int ld_x, const float *__restrict__ Xp) {
@@ -398,12 +429,21 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
   const size_t wbytes = (size_t)Kp * Np * 4;
   uint8_t *whi = base, *wlo = base + wbytes;
   uint8_t *stg = base + 2 * wbytes;                                         // nst x (hi, lo) boxes
-  float *epi = reinterpret_cast<float *>(stg + (size_t)nst * 2 * NT_BOX_BYTES);  // 4 warps x 32 x 32 floats
+  float *epi = reinterpret_cast<float *>(stg + (size_t)nst * 2 * NT_BOX_BYTES);  // 4 warps x ebuf x 32 x 32 floats
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (R + NT_BM - 1) / NT_BM;
   const int my_tiles = blockIdx.x < ntiles ? static_cast<int>((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
   const int G = my_tiles * kchunks;
+  const int pre = min(nst, G);  // boxes in flight before W is staged
   volatile int *vfail = &s_fail;
+  auto box_hi = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES; };
+  auto box_lo = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES + NT_BOX_BYTES; };
+  auto issue = [&](int g) {
+    const int s = g % nst, tl = g / kchunks, kc = g % kchunks;
+    const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
+    mbar_expect_tx(&full_bar[s], NT_BOX_BYTES);
+    tma_load_2d(box_hi(s), &xmap, kc * NT_KC, static_cast<int>(tile * NT_BM), &full_bar[s]);
+  };
 
   if (tid == 0) {
     for (int s = 0; s < nst; ++s) {
@@ -417,21 +457,33 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
     }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the first boxes do not depend on W: their copies overlap its staging
+    for (int g = 0; g < pre; ++g) issue(g);
   }
   if (wid == 0) {
+    __syncwarp();
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // W^T (N_p x K_p, K-major, 128-byte swizzle) as hi and lo: element (n, k) of
   // column block kc at kc * N_p * 128 + (n / 8) * 1024 + (n % 8) * 128 +
-  // (((k % 32) / 4) ^ (n % 8)) * 16 + (k % 4) * 4
-  for (int k = wid; k < Kp; k += NW_THREADS / 32) {
-    const int kc = k / NT_KC, kl = k % NT_KC;
-    for (int n = lane; n < Np; n += 32) {
-      const float w = (k < K && n < N) ? W[(int64_t)k * ld_w + n] : 0.f;
+  // (((k % 32) / 4) ^ (n % 8)) * 16 + (k % 4) * 4.  Eight loads per thread are
+  // in flight before their values are split and stored.
+  for (int e0 = tid; e0 < Kp * Np; e0 += 8 * NW_THREADS) {
+    float w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * NW_THREADS, k = e / Np, n = e % Np;
+      w[u] = (e < Kp * Np && k < K && n < N) ? W[(int64_t)k * ld_w + n] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * NW_THREADS, k = e / Np, n = e % Np;
+      if (e >= Kp * Np) break;
+      const int kc = k / NT_KC, kl = k % NT_KC;
       float h, lw;
-      tf32_split(w, h, lw);
+      tf32_split(w[u], h, lw);
       const size_t off =
           (size_t)kc * Np * 128 + (n >> 3) * 1024 + (n & 7) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
       *reinterpret_cast<float *>(whi + off) = h;
@@ -443,24 +495,19 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
-  auto box_hi = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES; };
-  auto box_lo = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES + NT_BOX_BYTES; };
   const unsigned fullm = 0xffffffffu;
   if (wid == 0) {
     // ---- TMA producer ----
     if (lane == 0) {
-      int issued = 0;
-      for (int g = 0; g < G; ++g) {
+      int issued = pre;
+      for (int g = pre; g < G; ++g) {
         if (failed(vfail)) break;
         const int s = g % nst;
-        if (g >= nst && !mbar_wait(&empty_bar[s], ((g / nst) - 1) & 1)) {
+        if (!mbar_wait(&empty_bar[s], ((g / nst) - 1) & 1)) {
           atomicOr(&s_fail, 1);
           break;
         }
-        const int tl = g / kchunks, kc = g % kchunks;
-        const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
-        mbar_expect_tx(&full_bar[s], NT_BOX_BYTES);
-        tma_load_2d(box_hi(s), &xmap, kc * NT_KC, static_cast<int>(tile * NT_BM), &full_bar[s]);
+        issue(g);
         issued = g + 1;
       }
       // every issued copy lands before the block exits: the last one per stage
@@ -534,8 +581,9 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
   } else if (wid >= 12) {
     // ---- epilogue: accumulator rows 32 (w % 4) .. + 31 of each tile ----
     const int ew = wid - 12;
-    float4 *buf4 = reinterpret_cast<float4 *>(epi) + ew * 32 * 8;  // 32 rows x 8 float4
     const bool vec_out = ld_z % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15u) == 0;
+    int chunk = 0;         // 32-column chunks staged by this warp
+    bool pending = false;  // lane 0: bulk stores issued (their reads of the buffers may be in flight)
     for (int tl = 0; tl < my_tiles; ++tl) {
       if (__any_sync(fullm, failed(vfail))) break;
       const int a = tl & 1;
@@ -546,14 +594,45 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
       }
       tc_fence_after();
       const int64_t row0 = ((int64_t)blockIdx.x + (int64_t)tl * gridDim.x) * NT_BM + 32 * ew;
-      for (int c0 = 0; c0 < N; c0 += 32) {
+      for (int c0 = 0; c0 < N; c0 += 32, ++chunk) {
+        // 32 rows x 32 columns, row = lane, float4 q of a row at q ^ (row % 8):
+        // the 128-byte-swizzled box of the bulk tensor store
+        float *bf = epi + (size_t)(ew * ebuf + chunk % ebuf) * 1024;
+        float4 *buf4 = reinterpret_cast<float4 *>(bf);
+        if (zmode != 0) {
+          // the store that last read this buffer has finished reading it
+          if (lane == 0 && pending) {
+            if (ebuf == 2) bulk_wait_read<1>();
+            else bulk_wait_read<0>();
+          }
+          __syncwarp();
+        }
         for (int c = 0; c < 32 && c0 + c < N; c += 16) {
           float v[16];
           tmem_ld16(tmem + (static_cast<uint32_t>(32 * ew) << 16) + static_cast<uint32_t>(a * Np + c0 + c), v);
+          if (zmode != 0) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int col = c0 + c + k;
+              v[k] = col < N ? v[k] * alpha * (colscale ? colscale[col] : 1.0f) : 0.f;
+            }
+          }
 #pragma unroll
           for (int u = 0; u < 4; ++u)
             buf4[lane * 8 + (((c >> 2) + u) ^ (lane & 7))] =
                 make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        }
+        if (zmode != 0) {
+          fence_proxy_async();
+          __syncwarp();
+          // rows past R and columns past N are clipped by the tensor map
+          if (lane == 0 && row0 < R) {
+            if (zmode == 1) tma_store_2d(&zmap, bf, c0, static_cast<int>(row0));
+            else tma_add_2d(&zmap, bf, c0, static_cast<int>(row0));
+            bulk_commit();
+            pending = true;
+          }
+          continue;
         }
         __syncwarp();
         for (int e = lane; e < 32 * 8; e += 32) {
@@ -586,6 +665,8 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K,
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce_bar[a]);
     }
+    // every bulk store has completed before the block exits
+    if (lane == 0 && pending) bulk_wait_all<0>();
   }
   __syncthreads();
   tc_fence_after();
@@ -826,21 +907,27 @@ int tc_nsplit(int64_t R) {
 // ---- panel x small factor (tensor cores) --------------------------------------
 namespace {
 struct NtPlan {
-  int Kp, Np, nst;
+  int Kp, Np, nst, ebuf;
   uint32_t cols;
   size_t smem;
 };
-// W's hi and lo parts, a 16 KiB epilogue tile and as many (hi, lo) box stages
-// as fit (two to four); two accumulators of N_p columns in tensor memory
+// W's hi and lo parts, one or two 16 KiB epilogue staging tiles (two when
+// that still leaves two box stages) and as many (hi, lo) box stages as fit
+// (two to four); two accumulators of N_p columns in tensor memory
 NtPlan nt_plan(int K, int N) {
   NtPlan p{};
   p.Kp = static_cast<int>(round_up(K, NT_KC));
   p.Np = static_cast<int>(round_up(N, 16));
-  const size_t fixed = 2 * (size_t)p.Kp * p.Np * 4 + 16 * 1024 + 1024;
-  p.nst = fixed < NT_SMEM_LIMIT ? static_cast<int>(std::min<size_t>(NW_MAXST, (NT_SMEM_LIMIT - fixed) /
-                                                                                     (2 * NT_BOX_BYTES)))
-                                : 0;
-  p.smem = fixed + (size_t)p.nst * 2 * NT_BOX_BYTES;
+  const size_t wfix = 2 * (size_t)p.Kp * p.Np * 4 + 1024;
+  auto stages = [&](int ebuf) {
+    const size_t fixed = wfix + (size_t)ebuf * 16 * 1024;
+    return fixed < NT_SMEM_LIMIT ? static_cast<int>(std::min<size_t>(NW_MAXST, (NT_SMEM_LIMIT - fixed) /
+                                                                                  (2 * NT_BOX_BYTES)))
+                                 : 0;
+  };
+  p.ebuf = stages(2) >= 2 ? 2 : 1;
+  p.nst = stages(p.ebuf);
+  p.smem = wfix + (size_t)p.ebuf * 16 * 1024 + (size_t)p.nst * 2 * NT_BOX_BYTES;
   p.cols = 32;
   while (p.cols < static_cast<uint32_t>(2 * p.Np)) p.cols <<= 1;
   return p;
@@ -868,6 +955,20 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
                                   estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) fail(MC_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)cr));
+  // Z through bulk tensor stores (beta 0) or adds (beta 1) when a tensor map
+  // describes it: 16-byte aligned rows, at least one 32-column box wide
+  CUtensorMap zmap;
+  std::memset(&zmap, 0, sizeof(zmap));
+  int zmode = 0;
+  if ((beta == 0.f || beta == 1.f) && N >= 32 && ld_z % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15u) == 0) {
+    const cuuint64_t zdim[2] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(R)};
+    const cuuint64_t zstride[1] = {static_cast<cuuint64_t>(ld_z) * sizeof(float)};
+    const cuuint32_t zbox[2] = {32, 32};
+    if (encode_fn()(&zmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Z, zdim, zstride, zbox, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      zmode = beta == 0.f ? 1 : 2;
+  }
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -878,8 +979,9 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
   const int grid = static_cast<int>(std::min<int64_t>(ntiles, sms));
   MC_CUDA(cudaFuncSetAttribute(gemm_nn_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)NT_SMEM_LIMIT));
-  gemm_nn_tc_ws_kernel<<<grid, NW_THREADS, p.smem, st>>>(map, R, K, N, p.Kp, p.Np, p.cols, p.nst, W, ld_w, colscale,
-                                                          alpha, beta, Z, ld_z, err, copy_if, ld_x, X);
+  gemm_nn_tc_ws_kernel<<<grid, NW_THREADS, p.smem, st>>>(map, zmap, zmode, p.ebuf, R, K, N, p.Kp, p.Np, p.cols,
+                                                          p.nst, W, ld_w, colscale, alpha, beta, Z, ld_z, err,
+                                                          copy_if, ld_x, X);
   MC_CHECK_LAUNCH();
 }
 

@@ -240,13 +240,15 @@ def test_coo_ingest_matches_csr(mc):
 
 
 @pytest.mark.parametrize("R,K,N", [(138_000, 60, 60), (27_000, 240, 52), (50_001, 180, 60), (300, 7, 13),
-                                   (129, 32, 16), (5_000, 256, 64), (1_000, 64, 256)])
+                                   (129, 32, 16), (5_000, 256, 64), (1_000, 64, 256), (777, 40, 33)])
 def test_panel_gemm_tensor_cores(mc, R, K, N):
     """Z = X W on the tensor cores (3xTF32) against a float64 product: every
     entry within 1e-5 of max |X| |W| (the bound of a float32 sum over K terms
     with the TF32 split's error of about 2^-22 per product), and against the
     SIMT kernels.  Ragged R (not a multiple of the 128-row tile), K and N (not
-    multiples of the 32-column box or 16-column MMA) are covered."""
+    multiples of the 32-column box or 16-column MMA) are covered; at 777 x 33
+    the last 32-row output block starts past R (no store issued) and the
+    second 32-column store box holds one column."""
     rng = np.random.default_rng(R + K + N)
     X = rng.standard_normal((R, K)).astype(np.float32)
     W = (rng.standard_normal((K, N)) / np.sqrt(K)).astype(np.float32)
