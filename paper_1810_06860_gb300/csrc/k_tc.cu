@@ -438,8 +438,7 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
   volatile int *vfail = &s_fail;
   auto box_hi = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES; };
   auto box_lo = [&](int s) { return stg + (size_t)s * 2 * NT_BOX_BYTES + NT_BOX_BYTES; };
-  auto issue = [&](int g) {
-    const int s = g % nst, tl = g / kchunks, kc = g % kchunks;
+  auto issue = [&](int s, int kc, int tl) {
     const int64_t tile = blockIdx.x + (int64_t)tl * gridDim.x;
     mbar_expect_tx(&full_bar[s], NT_BOX_BYTES);
     tma_load_2d(box_hi(s), &xmap, kc * NT_KC, static_cast<int>(tile * NT_BM), &full_bar[s]);
@@ -458,7 +457,7 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // the first boxes do not depend on W: their copies overlap its staging
-    for (int g = 0; g < pre; ++g) issue(g);
+    for (int g = 0; g < pre; ++g) issue(g, g % kchunks, g / kchunks);
   }
   if (wid == 0) {
     __syncwarp();
@@ -499,16 +498,25 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
   if (wid == 0) {
     // ---- TMA producer ----
     if (lane == 0) {
-      int issued = pre;
+      // the loop runs only when pre == nst, so box g = pre reuses stage 0
+      int issued = pre, s = 0, kc = pre % kchunks, tl = pre / kchunks;
+      uint32_t eph = 0;
       for (int g = pre; g < G; ++g) {
         if (failed(vfail)) break;
-        const int s = g % nst;
-        if (!mbar_wait(&empty_bar[s], ((g / nst) - 1) & 1)) {
+        if (!mbar_wait(&empty_bar[s], eph)) {
           atomicOr(&s_fail, 1);
           break;
         }
-        issue(g);
+        issue(s, kc, tl);
         issued = g + 1;
+        if (++s == nst) {
+          s = 0;
+          eph ^= 1u;
+        }
+        if (++kc == kchunks) {
+          kc = 0;
+          ++tl;
+        }
       }
       // every issued copy lands before the block exits: the last one per stage
       // is the latest phase armed there (a completed one returns at once)
@@ -517,46 +525,63 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
   } else if (wid == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
+      // A single thread issues every MMA, so the loop keeps its stage, phase,
+      // chunk and tile counters incrementally and moves descriptors by adding
+      // address units (16 bytes) instead of rebuilding them.
       const uint32_t idesc = idesc_tf32(NT_BM, Np);
-      const uint32_t wstride = static_cast<uint32_t>(Np) * 128;
+      const uint64_t wstep = static_cast<uint64_t>(Np) * 128 >> 4;       // one 32-row block of W^T
+      const uint64_t xstep = static_cast<uint64_t>(2 * NT_BOX_BYTES) >> 4;  // one (hi, lo) stage
+      const uint64_t dwh = smem_desc(smem_u32(whi)), dwl = smem_desc(smem_u32(wlo)), dx = smem_desc(smem_u32(stg));
       int committed = -1;
+      uint32_t committed_ph = 0;
+      int s = 0, kc = 0, tl = 0;
+      uint32_t ph = 0;
       for (int g = 0; g < G; ++g) {
         if (failed(vfail)) break;
-        const int s = g % nst, tl = g / kchunks, kc = g % kchunks, a = tl & 1;
+        const int a = tl & 1;
         if (kc == 0 && tl >= 2 && !mbar_wait(&acce_bar[a], ((tl >> 1) - 1) & 1)) {
           atomicOr(&s_fail, 2);
           break;
         }
-        if (!mbar_wait(&split_bar[s], (g / nst) & 1)) {
+        if (!mbar_wait(&split_bar[s], ph)) {
           atomicOr(&s_fail, 4);
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem + static_cast<uint32_t>(a * Np);
-        const uint32_t ah = smem_u32(box_hi(s)), al = smem_u32(box_lo(s));
-        const uint32_t bh = smem_u32(whi) + kc * wstride, bl = smem_u32(wlo) + kc * wstride;
+        const uint64_t ah = dx + s * xstep, al = ah + (NT_BOX_BYTES >> 4);
+        const uint64_t bh = dwh + kc * wstep, bl = dwl + kc * wstep;
 #pragma unroll
         for (int ks = 0; ks < NT_KC / 8; ++ks) {
-          const uint32_t ko = ks * 32;
           const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(d, smem_desc(ah + ko), smem_desc(bh + ko), idesc, acc0);
-          mma_tf32(d, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
-          mma_tf32(d, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
+          mma_tf32(d, ah + 2 * ks, bh + 2 * ks, idesc, acc0);  // 8 columns = 32 bytes further
+          mma_tf32(d, ah + 2 * ks, bl + 2 * ks, idesc, 1u);
+          mma_tf32(d, al + 2 * ks, bh + 2 * ks, idesc, 1u);
         }
         mma_commit(&empty_bar[s]);
         if (kc == kchunks - 1) mma_commit(&accf_bar[a]);
-        committed = g;
+        committed = s;
+        committed_ph = ph;
+        if (++s == nst) {
+          s = 0;
+          ph ^= 1u;
+        }
+        if (++kc == kchunks) {
+          kc = 0;
+          ++tl;
+        }
       }
       // the last commit covers every MMA issued before it
-      if (committed >= 0 && !mbar_wait(&empty_bar[committed % nst], (committed / nst) & 1)) atomicOr(&s_fail, 64);
+      if (committed >= 0 && !mbar_wait(&empty_bar[committed], committed_ph)) atomicOr(&s_fail, 64);
     }
   } else if (wid >= 4 && wid < 12) {
     // ---- split into TF32 hi (in place) and float32 lo ----
     const int st = tid - 128;
-    for (int g = 0; g < G; ++g) {
+    int s = 0;
+    uint32_t ph = 0;
+    for (int g = 0; g < G; ++g, s = s + 1 == nst ? 0 : s + 1, ph ^= s == 0 ? 1u : 0u) {
       if (__any_sync(fullm, failed(vfail))) break;
-      const int s = g % nst;
-      const bool ok = mbar_wait(&full_bar[s], (g / nst) & 1);
+      const bool ok = mbar_wait(&full_bar[s], ph);
       if (!__all_sync(fullm, ok)) {
         atomicOr(&s_fail, 8);
         break;
@@ -753,64 +778,88 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
   if (wid == 0) {
     // ---- TMA producer ----
     if (lane == 0) {
-      int issued = 0;
-      for (int g = 0; g < S; ++g) {
+      int issued = 0, s = 0;
+      uint32_t ph = 0;  // parity of stage s's current use
+      int y = static_cast<int>(r0);
+      for (int g = 0; g < S; ++g, y += TT_KT) {
         if (failed(vfail)) break;
-        const int s = g % nst;
-        if (g >= nst && !mbar_wait(&rawfree_bar[s], ((g / nst) - 1) & 1)) {
+        if (g >= nst && !mbar_wait(&rawfree_bar[s], ph ^ 1u)) {
           atomicOr(&s_fail, 1);
           break;
         }
         mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(raw_bytes));
-        const int y = static_cast<int>(r0 + (int64_t)g * TT_KT);
         for (int j = 0; j < nbA; ++j) tma_load_2d(raw(s) + j * TT_BOX, &amap, 32 * j, y, &full_bar[s]);
         if (!same)
           for (int j = 0; j < nbB; ++j) tma_load_2d(raw(s) + (nbA + j) * TT_BOX, &bmap, 32 * j, y, &full_bar[s]);
         issued = g + 1;
+        if (++s == nst) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
       for (int g = max(0, issued - nst); g < issued; ++g) mbar_wait(&full_bar[g % nst], (g / nst) & 1);
     }
   } else if (wid == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
+      // one thread issues every MMA: incremental stage and phase, descriptors
+      // moved by adding address units (16 bytes)
       const uint32_t idesc = idesc_tf32(128, Np);
-      int committed = -1;
+      const uint64_t sstep = static_cast<uint64_t>(stage_bytes) >> 4;
+      const uint64_t dh0 = smem_desc(smem_u32(hi(0))), dl0 = smem_desc(smem_u32(lo(0)));
+      const uint64_t boff = same ? 0 : static_cast<uint64_t>(aboxes * TT_BOX) >> 4;
+      int committed = -1, ncommit = 0, s = 0;
+      uint32_t ph = 0, committed_ph = 0;
       for (int g = 0; g < S; ++g) {
         if (failed(vfail)) break;
-        const int s = g % nst;
-        if (!mbar_wait(&split_bar[s], (g / nst) & 1)) {
+        if (!mbar_wait(&split_bar[s], ph)) {
           atomicOr(&s_fail, 4);
           break;
         }
         tc_fence_after();
-        const uint32_t ah = smem_u32(hi(s)), al = smem_u32(lo(s));
-        const uint32_t bh = same ? ah : ah + aboxes * TT_BOX, bl = same ? al : al + aboxes * TT_BOX;
+        const uint64_t ah = dh0 + s * sstep, al = dl0 + s * sstep, bh = ah + boff, bl = al + boff;
+        if (mt == 1) {
 #pragma unroll
-        for (int ks = 0; ks < TT_KT / 8; ++ks) {
-          const uint32_t ko = ks * 32;
-          const uint32_t acc0 = (g > 0 || ks > 0) ? 1u : 0u;
-          for (int t = 0; t < mt; ++t) {
-            const uint32_t d = tmem + static_cast<uint32_t>(t * Np);
-            const uint32_t ao = static_cast<uint32_t>(t) * 16 * 1024 + ko;  // 128 columns = 16 atoms further
-            mma_tf32(d, smem_desc(ah + ao), smem_desc(bh + ko), idesc, acc0);
-            mma_tf32(d, smem_desc(ah + ao), smem_desc(bl + ko), idesc, 1u);
-            mma_tf32(d, smem_desc(al + ao), smem_desc(bh + ko), idesc, 1u);
+          for (int ks = 0; ks < TT_KT / 8; ++ks) {
+            const uint32_t acc0 = (g > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32(tmem, ah + 2 * ks, bh + 2 * ks, idesc, acc0);  // 8 rows = 32 bytes further
+            mma_tf32(tmem, ah + 2 * ks, bl + 2 * ks, idesc, 1u);
+            mma_tf32(tmem, al + 2 * ks, bh + 2 * ks, idesc, 1u);
+          }
+        } else {
+#pragma unroll
+          for (int ks = 0; ks < TT_KT / 8; ++ks) {
+            const uint32_t acc0 = (g > 0 || ks > 0) ? 1u : 0u;
+            for (int t = 0; t < mt; ++t) {
+              const uint32_t d = tmem + static_cast<uint32_t>(t * Np);
+              const uint64_t ao = static_cast<uint64_t>(t) * 1024 + 2 * ks;  // 128 columns = 16 KiB further
+              mma_tf32(d, ah + ao, bh + 2 * ks, idesc, acc0);
+              mma_tf32(d, ah + ao, bl + 2 * ks, idesc, 1u);
+              mma_tf32(d, al + ao, bh + 2 * ks, idesc, 1u);
+            }
           }
         }
         mma_commit(&splitfree_bar[s]);
-        committed = g;
+        committed = s;
+        committed_ph = ph;
+        ++ncommit;
+        if (++s == nst) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
-      if (S > 0 && committed == S - 1) mma_commit(&acc_bar);
-      if (committed >= 0 && !mbar_wait(&splitfree_bar[committed % nst], (committed / nst) & 1)) atomicOr(&s_fail, 8);
+      if (S > 0 && ncommit == S) mma_commit(&acc_bar);
+      if (committed >= 0 && !mbar_wait(&splitfree_bar[committed], committed_ph)) atomicOr(&s_fail, 8);
     }
   } else if (wid >= 4) {
     // ---- transpose and split ----
     const int st = tid - 128;
-    for (int g = 0; g < S; ++g) {
+    int s = 0;
+    uint32_t ph = 0;
+    for (int g = 0; g < S; ++g, s = s + 1 == nst ? 0 : s + 1, ph ^= s == 0 ? 1u : 0u) {
       if (__any_sync(fullm, failed(vfail))) break;
-      const int s = g % nst;
-      bool ok = mbar_wait(&full_bar[s], (g / nst) & 1);
-      if (ok && g >= nst) ok = mbar_wait(&splitfree_bar[s], ((g / nst) - 1) & 1);
+      bool ok = mbar_wait(&full_bar[s], ph);
+      if (ok && g >= nst) ok = mbar_wait(&splitfree_bar[s], ph ^ 1u);
       if (!__all_sync(fullm, ok)) {
         atomicOr(&s_fail, 2);
         break;
