@@ -199,6 +199,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (wid == 0) {
+    __syncwarp();
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -281,7 +282,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
         issued = s + 3;
       }
     }
+    __syncwarp();  // warp 0 reconverges after thread 0's issue
   }
+  __syncwarp();
   __syncthreads();
   if (tid == 0) {
     // The last commit covers every MMA issued before it: wait for it.  Then
@@ -291,6 +294,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t R, int K, int n
     if (committed >= 0 && !mbar_wait(&mma_bar[committed & 1], (committed >> 1) & 1)) atomicOr(&s_fail, 2);
     for (int t = committed + 1; t < issued; ++t) mbar_wait(&full_bar[t & 1], (t >> 1) & 1);
   }
+  __syncwarp();
   __syncthreads();
   // read the accumulators only after a complete run
   const bool have = S > 0 && !s_fail;
@@ -693,6 +697,10 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
     // every bulk store has completed before the block exits
     if (lane == 0 && pending) bulk_wait_all<0>();
   }
+  // The producer and issuer roles ran on lane 0 alone: the warp reconverges
+  // before the block barrier, which must count every warp only once it has
+  // left its role (the tensor memory is freed after it).
+  __syncwarp();
   __syncthreads();
   tc_fence_after();
   if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
@@ -764,6 +772,7 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (wid == 0) {
+    __syncwarp();
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -896,6 +905,7 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
       }
     }
   }
+  __syncwarp();  // lanes 1..31 of the producer and issuer warps wait for lane 0
   __syncthreads();
   if (wid >= 8) {
     // ---- partial tile: accumulator t holds rows 128 t .. of C, lane = row ----
