@@ -580,6 +580,114 @@ chol_inv_small_kernel(int K, const float *__restrict__ G, int ld, float shift_re
   }
 }
 
+// ============================================== chol_inv (K <= 64) =======
+// The same factorisation and inverse as chol_inv_small_kernel, register
+// resident: thread a keeps row a of the trailing matrix A and row a of the
+// running right-hand side B (B = I at the start; row j of B ends as row j of
+// L^{-1}).  Step j: every row a >= j publishes A[a][j] (column j, the pivot
+// A[j][j] among it) and row j publishes its row of B scaled by the pivot's
+// 1/sqrt; after one barrier every thread forms L[a][j] = A[a][j] / sqrt(A[j][j])
+// and L[b][j] the same way, and updates A[a][b] -= L[a][j] L[b][j] (b > j) and
+// B[a][b] -= L[a][j] B[j][b] (b <= j): the arithmetic of the shared-memory
+// kernel, one barrier per step instead of two, no shared-memory updates.  The
+// published column and row alternate between two buffers, so step j + 1 never
+// overwrites what a slower thread still reads for step j.
+template <int KP>
+__global__ void __launch_bounds__(KP, 1)
+chol_inv_reg_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
+                    float ref_tol, float *__restrict__ Rinv, const int *__restrict__ skip_if,
+                    int *__restrict__ set_skip, float skip3) {
+  __shared__ float colb[2][KP], browb[2][KP], flags[KP];
+  __shared__ float red_tr[KP / 32], red_mx[KP / 32], red_dev[KP / 32];
+  if (skip_if && *skip_if) return;  // a pass the previous one made unnecessary
+  const int a = threadIdx.x, lane = a & 31, w = a >> 5;
+  const bool mine = a < K;
+  // trace and largest diagonal entry (the shift and the drop threshold)
+  const float ga = mine ? G[(int64_t)a * ld + a] : 0.f;
+  float tr = ga, mx = ga;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, off);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  if (lane == 0) {
+    red_tr[w] = tr;
+    red_mx[w] = mx;
+  }
+  // a column that lost (almost) all of its norm to an earlier projection is
+  // rounding noise: it is removed before factoring
+  flags[a] = (!mine || (ref_diag && !(ga > ref_tol * ref_diag[a]))) ? 0.f : 1.f;
+  __syncthreads();
+  float s_tr = 0.f, s_max = 0.f;
+#pragma unroll
+  for (int i = 0; i < KP / 32; ++i) {
+    s_tr += red_tr[i];
+    s_max = fmaxf(s_max, red_mx[i]);
+  }
+  const float shift = shift_rel * s_tr / K;
+  const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
+  const bool live_a = flags[a] != 0.f;
+  float A[KP], B[KP];
+  float dev = 0.f;  // largest |G - I| over the lower triangle
+#pragma unroll
+  for (int b = 0; b < KP; ++b) {
+    const float g = (mine && b <= a) ? G[(int64_t)a * ld + b] : 0.f;
+    if (mine && b <= a) dev = fmaxf(dev, fabsf(g - (a == b ? 1.f : 0.f)));
+    A[b] = (b <= a && live_a && flags[b] != 0.f) ? g + (a == b ? shift : 0.f) : 0.f;
+    B[b] = a == b ? 1.f : 0.f;
+  }
+  if (set_skip) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, off));
+    if (lane == 0) red_dev[w] = dev;
+  }
+  // step j; the two constant-trip loops below unroll completely, so every
+  // index into A and B is a constant and both stay in registers
+  auto step = [&](const int j) {
+    if (j >= K) return;
+    float *col = colb[j & 1], *brow = browb[j & 1];
+    if (a >= j) col[a] = A[j];
+    if (a == j) {
+      const float inv = A[j] > drop ? rsqrtf(A[j]) : 0.f;
+#pragma unroll
+      for (int b = 0; b <= j; ++b) brow[b] = B[b] * inv;
+      if (!(A[j] > drop)) flags[j] = 0.f;
+    }
+    __syncthreads();
+    const float d = col[j];
+    const float inv = d > drop ? rsqrtf(d) : 0.f;
+    if (a == j) {
+#pragma unroll
+      for (int b = 0; b <= j; ++b) B[b] = brow[b];
+    } else if (a > j && inv != 0.f) {
+      const float la = A[j] * inv;
+#pragma unroll
+      for (int b = j + 1; b < KP; ++b) A[b] -= la * (col[b] * inv);  // entries b > a are never read
+#pragma unroll
+      for (int b = 0; b <= j; ++b) B[b] -= la * brow[b];
+    }
+  };
+#pragma unroll
+  for (int j = 0; j < (KP < 32 ? KP : 32); ++j) step(j);
+#pragma unroll
+  for (int j = 32; j < KP; ++j) step(j);
+  __syncthreads();
+  if (set_skip && a == 0) {
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < KP / 32; ++i) d = fmaxf(d, red_dev[i]);
+    *set_skip = d <= skip3 ? 1 : 0;
+  }
+  // R^{-1} = (L^{-1})^T: thread a writes column a, R^{-1}[i][a] = B[a][i] for
+  // i <= a; rows and columns of dropped pivots are zero
+  if (mine) {
+    const bool fa = flags[a] != 0.f;
+#pragma unroll
+    for (int i = 0; i < KP; ++i)
+      if (i < K) Rinv[(int64_t)i * K + a] = (fa && i <= a && flags[i] != 0.f) ? B[i] : 0.f;
+  }
+}
+
 // =========================================================== chol_inv ======
 // One block.  G + shift I = L L^T (right-looking, warp per row of the trailing
 // update); pivots below the drop threshold make their column "absent": its
@@ -1284,9 +1392,27 @@ float skip3_tol() {
   return v;
 }
 
+// The register-resident factorisation for K <= 64 (MC_CHOL_REG=0: the
+// shared-memory kernel for every K <= 128).
+bool use_chol_reg() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_CHOL_REG");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag, float ref_tol,
               float *Rinv, const int *skip_if, int *set_skip) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
+  if (K <= 64 && use_chol_reg()) {
+    if (K <= 32) chol_inv_reg_kernel<32><<<1, 32, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if,
+                                                           set_skip, skip3_tol());
+    else chol_inv_reg_kernel<64><<<1, 64, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip,
+                                                   skip3_tol());
+    MC_CHECK_LAUNCH();
+    return;
+  }
   if (K <= 128) {
     const int ls = (K % 2 == 0) ? K + 1 : K;
     const size_t need = sizeof(float) * (2 * (size_t)K * ls + K);
