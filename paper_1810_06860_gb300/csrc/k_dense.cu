@@ -581,110 +581,183 @@ chol_inv_small_kernel(int K, const float *__restrict__ G, int ld, float shift_re
 }
 
 // ============================================== chol_inv (K <= 64) =======
-// The same factorisation and inverse as chol_inv_small_kernel, register
-// resident: thread a keeps row a of the trailing matrix A and row a of the
-// running right-hand side B (B = I at the start; row j of B ends as row j of
-// L^{-1}).  Step j: every row a >= j publishes A[a][j] (column j, the pivot
-// A[j][j] among it) and row j publishes its row of B scaled by the pivot's
-// 1/sqrt; after one barrier every thread forms L[a][j] = A[a][j] / sqrt(A[j][j])
-// and L[b][j] the same way, and updates A[a][b] -= L[a][j] L[b][j] (b > j) and
-// B[a][b] -= L[a][j] B[j][b] (b <= j): the arithmetic of the shared-memory
-// kernel, one barrier per step instead of two, no shared-memory updates.  The
-// published column and row alternate between two buffers, so step j + 1 never
-// overwrites what a slower thread still reads for step j.
-template <int KP>
-__global__ void __launch_bounds__(KP, 1)
-chol_inv_reg_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
+// The factorisation and inverse of chol_inv_small_kernel for K <= 64, with
+// the same rounding (every entry takes its updates one fused multiply-add at
+// a time, in pivot order), arranged for latency: the matrix is padded to 64
+// with an identity block and factored in four 16-column blocks,
+//   (1) the diagonal block by one warp, lane a holding row a in registers and
+//       the column of each step passed by shuffles;
+//   (2) the rows below it by a thread per row, registers again, the block's
+//       L read as shared-memory broadcasts;
+//   (3) the trailing matrix's rank-16 update by a thread per entry;
+// three barriers per block.  L^{-1} follows by columns, four threads (one
+// warp's lanes 4c'..4c'+3) per column holding its rows i = r (mod 4) in
+// registers: step k scales entry (k, c) by the pivot's 1/sqrt and shuffles
+// it to the other three, which update their rows i > k.  Pivots at or below
+// the drop threshold give a zero column of L and a zero row of L^{-1}.
+constexpr int CB_K = 64, CB_NB = 16, CB_THREADS = 256;
+__global__ void __launch_bounds__(CB_THREADS)
+chol_inv_blk_kernel(int K, const float *__restrict__ G, int ld, float shift_rel, const float *__restrict__ ref_diag,
                     float ref_tol, float *__restrict__ Rinv, const int *__restrict__ skip_if,
                     int *__restrict__ set_skip, float skip3) {
-  __shared__ float colb[2][KP], browb[2][KP], flags[KP];
-  __shared__ float red_tr[KP / 32], red_mx[KP / 32], red_dev[KP / 32];
+  __shared__ float As[CB_K][CB_K + 1];  // lower triangle: A, then L (its diagonal keeps the pivot)
+  __shared__ float invd[CB_K], flags[CB_K], diagv[CB_K];
+  __shared__ float s_tr, s_max;
+  __shared__ unsigned s_dev;
   if (skip_if && *skip_if) return;  // a pass the previous one made unnecessary
-  const int a = threadIdx.x, lane = a & 31, w = a >> 5;
-  const bool mine = a < K;
-  // trace and largest diagonal entry (the shift and the drop threshold)
-  const float ga = mine ? G[(int64_t)a * ld + a] : 0.f;
-  float tr = ga, mx = ga;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned full = 0xffffffffu;
+  // every load in flight at once: entry (i, j) = (e / 64, e % 64), e = tid + 256 u
+  float g[16];
+  float dev = 0.f;  // largest |G - I| over the lower triangle
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    tr += __shfl_xor_sync(0xffffffffu, tr, off);
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  for (int u = 0; u < 16; ++u) {
+    const int e = tid + CB_THREADS * u, i = e >> 6, j = e & 63;
+    g[u] = (i < K && j <= i) ? G[(int64_t)i * ld + j] : 0.f;
   }
-  if (lane == 0) {
-    red_tr[w] = tr;
-    red_mx[w] = mx;
+  const float rd = (ref_diag && tid < K) ? ref_diag[tid] : 0.f;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int e = tid + CB_THREADS * u, i = e >> 6, j = e & 63;
+    if (i < K && j <= i) dev = fmaxf(dev, fabsf(g[u] - (i == j ? 1.f : 0.f)));
+    if (i == j && i < K) diagv[i] = g[u];
+  }
+  if (tid == 0) s_dev = 0u;
+  __syncthreads();
+  if (wid == 0) {
+    float tr = 0.f, mx = 0.f;
+    for (int i = lane; i < K; i += 32) {
+      tr += diagv[i];
+      mx = fmaxf(mx, diagv[i]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      tr += __shfl_xor_sync(full, tr, off);
+      mx = fmaxf(mx, __shfl_xor_sync(full, mx, off));
+    }
+    if (lane == 0) {
+      s_tr = tr;
+      s_max = mx;
+    }
   }
   // a column that lost (almost) all of its norm to an earlier projection is
   // rounding noise: it is removed before factoring
-  flags[a] = (!mine || (ref_diag && !(ga > ref_tol * ref_diag[a]))) ? 0.f : 1.f;
-  __syncthreads();
-  float s_tr = 0.f, s_max = 0.f;
-#pragma unroll
-  for (int i = 0; i < KP / 32; ++i) {
-    s_tr += red_tr[i];
-    s_max = fmaxf(s_max, red_mx[i]);
-  }
-  const float shift = shift_rel * s_tr / K;
-  const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
-  const bool live_a = flags[a] != 0.f;
-  float A[KP], B[KP];
-  float dev = 0.f;  // largest |G - I| over the lower triangle
-#pragma unroll
-  for (int b = 0; b < KP; ++b) {
-    const float g = (mine && b <= a) ? G[(int64_t)a * ld + b] : 0.f;
-    if (mine && b <= a) dev = fmaxf(dev, fabsf(g - (a == b ? 1.f : 0.f)));
-    A[b] = (b <= a && live_a && flags[b] != 0.f) ? g + (a == b ? shift : 0.f) : 0.f;
-    B[b] = a == b ? 1.f : 0.f;
-  }
+  if (tid < CB_K) flags[tid] = (tid < K && ref_diag && !(diagv[tid] > ref_tol * rd)) ? 0.f : 1.f;
   if (set_skip) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, off));
-    if (lane == 0) red_dev[w] = dev;
+    for (int off = 16; off > 0; off >>= 1) dev = fmaxf(dev, __shfl_xor_sync(full, dev, off));
+    if (lane == 0) atomicMax(&s_dev, __float_as_uint(dev));  // nonnegative floats order as their bits
   }
-  // step j; the two constant-trip loops below unroll completely, so every
-  // index into A and B is a constant and both stay in registers
-  auto step = [&](const int j) {
-    if (j >= K) return;
-    float *col = colb[j & 1], *brow = browb[j & 1];
-    if (a >= j) col[a] = A[j];
-    if (a == j) {
-      const float inv = A[j] > drop ? rsqrtf(A[j]) : 0.f;
+  __syncthreads();
+  if (set_skip && tid == 0) *set_skip = __uint_as_float(s_dev) <= skip3 ? 1 : 0;
+  const float shift = shift_rel * s_tr / K;
+  const float drop = fmaxf(1e-30f, 1e-12f * s_max) + shift;
 #pragma unroll
-      for (int b = 0; b <= j; ++b) brow[b] = B[b] * inv;
-      if (!(A[j] > drop)) flags[j] = 0.f;
+  for (int u = 0; u < 16; ++u) {
+    const int e = tid + CB_THREADS * u, i = e >> 6, j = e & 63;
+    if (j > i) continue;
+    if (i < K) As[i][j] = (flags[i] != 0.f && flags[j] != 0.f) ? g[u] + (i == j ? shift : 0.f) : 0.f;
+    else As[i][j] = i == j ? 1.f : 0.f;  // padding: an identity block, coupled to nothing
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < CB_K; j0 += CB_NB) {
+    // (1) the diagonal block: lane a (and a + 16) holds row j0 + a
+    if (wid == 0) {
+      const int a = lane & 15;
+      float r[CB_NB];
+#pragma unroll
+      for (int b = 0; b < CB_NB; ++b) r[b] = b <= a ? As[j0 + a][j0 + b] : 0.f;
+      auto diag_step = [&](const int j) {
+        const float pj = __shfl_sync(full, r[j], j);
+        const bool keep = pj > drop;
+        const float inv = keep ? rsqrtf(pj) : 0.f;
+        if (a > j) r[j] *= inv;
+        const float la = r[j];
+#pragma unroll
+        for (int b = j + 1; b < CB_NB; ++b) {
+          const float lb = __shfl_sync(full, la, b);
+          if (a >= b) r[b] = fmaf(-la, lb, r[b]);
+        }
+        if (lane == 0) {
+          invd[j0 + j] = inv;
+          if (!keep) flags[j0 + j] = 0.f;
+        }
+      };
+#pragma unroll
+      for (int j = 0; j < 8; ++j) diag_step(j);
+#pragma unroll
+      for (int j = 8; j < CB_NB; ++j) diag_step(j);
+      if (lane < CB_NB) {
+#pragma unroll
+        for (int b = 0; b < CB_NB; ++b)
+          if (b <= a) As[j0 + a][j0 + b] = r[b];
+      }
     }
     __syncthreads();
-    const float d = col[j];
-    const float inv = d > drop ? rsqrtf(d) : 0.f;
-    if (a == j) {
+    // (2) the rows below it
+    const int j1 = j0 + CB_NB;
+    if (j1 + tid < CB_K) {
+      const int a = j1 + tid;
+      float r[CB_NB];
 #pragma unroll
-      for (int b = 0; b <= j; ++b) B[b] = brow[b];
-    } else if (a > j && inv != 0.f) {
-      const float la = A[j] * inv;
+      for (int b = 0; b < CB_NB; ++b) r[b] = As[a][j0 + b];
 #pragma unroll
-      for (int b = j + 1; b < KP; ++b) A[b] -= la * (col[b] * inv);  // entries b > a are never read
+      for (int j = 0; j < CB_NB; ++j) {
+        const float l = r[j] * invd[j0 + j];
+        r[j] = l;
 #pragma unroll
-      for (int b = 0; b <= j; ++b) B[b] -= la * brow[b];
+        for (int b = j + 1; b < CB_NB; ++b) r[b] = fmaf(-l, As[j0 + b][j0 + j], r[b]);
+      }
+#pragma unroll
+      for (int b = 0; b < CB_NB; ++b) As[a][j0 + b] = r[b];
+    }
+    __syncthreads();
+    // (3) the trailing matrix
+    if (j1 < CB_K) {
+#pragma unroll 4
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + CB_THREADS * u, a = e >> 6, b = e & 63;
+        if (b < j1 || b > a) continue;
+        float v = As[a][b];
+#pragma unroll
+        for (int k = 0; k < CB_NB; ++k) v = fmaf(-As[a][j0 + k], As[b][j0 + k], v);
+        As[a][b] = v;
+      }
+    }
+    __syncthreads();
+  }
+  // L^{-1}: thread (c, r) holds entries (4q + r, c); at step k entry (k, c) is
+  // final once scaled, and the rows below take its multiple
+  const int c = tid >> 2, r = tid & 3, src0 = lane & ~3;
+  float v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = 4 * q + r == c ? 1.f : 0.f;
+  auto inv_step = [&](const int k) {
+    if (r == (k & 3)) v[k >> 2] *= invd[k];
+    const float x = __shfl_sync(full, v[k >> 2], src0 | (k & 3));
+#pragma unroll
+    for (int q = k >> 2; q < 16; ++q) {
+      const int i = 4 * q + r;
+      if (i > k) v[q] = fmaf(-As[i][k], x, v[q]);
     }
   };
+  // four constant-trip loops unroll completely: every index into v is a constant
 #pragma unroll
-  for (int j = 0; j < (KP < 32 ? KP : 32); ++j) step(j);
+  for (int k = 0; k < 16; ++k) inv_step(k);
 #pragma unroll
-  for (int j = 32; j < KP; ++j) step(j);
-  __syncthreads();
-  if (set_skip && a == 0) {
-    float d = 0.f;
+  for (int k = 16; k < 32; ++k) inv_step(k);
 #pragma unroll
-    for (int i = 0; i < KP / 32; ++i) d = fmaxf(d, red_dev[i]);
-    *set_skip = d <= skip3 ? 1 : 0;
-  }
-  // R^{-1} = (L^{-1})^T: thread a writes column a, R^{-1}[i][a] = B[a][i] for
-  // i <= a; rows and columns of dropped pivots are zero
-  if (mine) {
-    const bool fa = flags[a] != 0.f;
+  for (int k = 32; k < 48; ++k) inv_step(k);
 #pragma unroll
-    for (int i = 0; i < KP; ++i)
-      if (i < K) Rinv[(int64_t)i * K + a] = (fa && i <= a && flags[i] != 0.f) ? B[i] : 0.f;
+  for (int k = 48; k < 64; ++k) inv_step(k);
+  // R^{-1} = (L^{-1})^T: row c of R^{-1} is column c of L^{-1}; rows and
+  // columns of dropped pivots are zero
+  if (c < K) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int rho = 4 * q + r;
+      if (rho < K) Rinv[(int64_t)c * K + rho] = (rho >= c && flags[c] != 0.f && flags[rho] != 0.f) ? v[q] : 0.f;
+    }
   }
 }
 
@@ -1392,11 +1465,11 @@ float skip3_tol() {
   return v;
 }
 
-// The register-resident factorisation for K <= 64 (MC_CHOL_REG=0: the
+// The blocked factorisation for K <= 64 (MC_CHOL_BLK=0: the unblocked
 // shared-memory kernel for every K <= 128).
-bool use_chol_reg() {
+bool use_chol_blk() {
   static const bool on = [] {
-    const char *v = std::getenv("MC_CHOL_REG");
+    const char *v = std::getenv("MC_CHOL_BLK");
     return !(v && v[0] == '0');
   }();
   return on;
@@ -1405,11 +1478,9 @@ bool use_chol_reg() {
 void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, const float *ref_diag, float ref_tol,
               float *Rinv, const int *skip_if, int *set_skip) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
-  if (K <= 64 && use_chol_reg()) {
-    if (K <= 32) chol_inv_reg_kernel<32><<<1, 32, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if,
-                                                           set_skip, skip3_tol());
-    else chol_inv_reg_kernel<64><<<1, 64, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip,
-                                                   skip3_tol());
+  if (K <= CB_K && use_chol_blk()) {
+    chol_inv_blk_kernel<<<1, CB_THREADS, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip,
+                                                  skip3_tol());
     MC_CHECK_LAUNCH();
     return;
   }
