@@ -330,7 +330,8 @@ eig_tridiag_mid_kernel(int K, const float *__restrict__ A, int lda, float *__res
 // to column c (summed across the lanes of the warp by a shuffle reduce-
 // scatter).  A thread per row finishes p and the dot v.p, and every thread
 // applies A -= v w^T + w v^T to its elements.  Three barriers per step; only
-// columns of the trailing block (c > j) are visited, a warp-uniform test.
+// columns of the trailing block (c > j) and blocks of 32 rows that reach
+// into it are visited, warp-uniform tests.
 // Outputs (d, e, beta, reflectors in Hv) as eig_tridiag_kernel.
 constexpr int TR_K = 256, TR_THREADS = 512, TR_NW = TR_THREADS / 32;
 constexpr int TR_A = 8, TR_B = 16;
@@ -459,6 +460,7 @@ eig_tridiag_reg_kernel(int K, const float *__restrict__ A, int lda, float *__res
 #pragma unroll
         for (int a = 0; a < TR_A; ++a) {
           if (b > 2 * a + 1) continue;
+          if (32 * a + 31 <= j) continue;  // rows l + 32 a all outside the trailing block (warp-uniform)
           const float e = x[a][b];
           rp[a] = fmaf(e, vc, rp[a]);
           // the diagonal element (r == c) contributes once, to its row
@@ -528,6 +530,7 @@ eig_tridiag_reg_kernel(int K, const float *__restrict__ A, int lda, float *__res
 #pragma unroll
         for (int a = 0; a < TR_A; ++a) {
           if (b > 2 * a + 1) continue;
+          if (32 * a + 31 <= j) continue;  // rows that no later step reads
           const bool keep = b < 2 * a || (b == 2 * a ? l >= w : l >= w + 16);
           if (keep) x[a][b] -= vr[a] * wc + wr[a] * vc;
         }

@@ -420,19 +420,23 @@ __global__ void spmm_fixup_kernel(int64_t nsplit, const int *__restrict__ split_
   }
 }
 
-// The same sums with a warp per split row for panels of at most 4 KM4
-// columns: every column group's partials are loaded in one pass over the
-// row's segments (K4 float4 per segment and lane), so the launch has a
-// third (K = 12) as many warps, each with the same few load latencies.  Per
-// column the order is that of spmm_fixup_kernel: the same bits.
+// The same sums with a warp per split row and chunk of KM4 column groups
+// (one chunk for panels of at most 4 KM4 columns): each lane loads a chunk
+// of a segment's partial row (KM4 consecutive float4) in one pass over the
+// row's segments, so the launch has fewer warps than column groups, each
+// with the same few load latencies, and a segment's row is read in whole
+// sectors.  Per column the order is that of spmm_fixup_kernel: the same bits.
 template <int KM4>
 __global__ void spmm_fixup_rows_kernel(int64_t nsplit, const int *__restrict__ split_row,
                                        const int *__restrict__ split_slot, const float *__restrict__ partial, int K,
-                                       float *__restrict__ out, int ld_out) {
-  const int K4 = K / 4;
+                                       float *__restrict__ out, int ld_out, int nchunk) {
   const int lane = threadIdx.x & 31;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nsplit; i += wstride) {
+  for (int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wi < nsplit * nchunk; wi += wstride) {
+    const int64_t i = wi / nchunk;
+    const int cb = static_cast<int>(wi - i * nchunk) * KM4;  // first column group of the chunk
+    const int K4 = K / 4 - cb;                               // column groups from cb on
+    const float *part_c = partial + 4 * cb;
     const int s0 = split_slot[i], s1 = split_slot[i + 1];
     float4 acc[KM4];
 #pragma unroll
@@ -444,7 +448,7 @@ __global__ void spmm_fixup_rows_kernel(int64_t nsplit, const int *__restrict__ s
         const int sg = b + 32 * u;
 #pragma unroll
         for (int c = 0; c < KM4; ++c)
-          v[u][c] = (sg < s1 && c < K4) ? *reinterpret_cast<const float4 *>(partial + (int64_t)sg * K + 4 * c)
+          v[u][c] = (sg < s1 && c < K4) ? *reinterpret_cast<const float4 *>(part_c + (int64_t)sg * K + 4 * c)
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
@@ -468,7 +472,7 @@ __global__ void spmm_fixup_rows_kernel(int64_t nsplit, const int *__restrict__ s
       }
     }
     if (lane == 0) {
-      float4 *dst = reinterpret_cast<float4 *>(out + (int64_t)split_row[i] * ld_out);
+      float4 *dst = reinterpret_cast<float4 *>(out + (int64_t)split_row[i] * ld_out + 4 * cb);
 #pragma unroll
       for (int c = 0; c < KM4; ++c)
         if (c < K4) dst[c] = acc[c];
@@ -746,19 +750,31 @@ void launch_seg(int u, int64_t blocks, int threads, cudaStream_t st, int64_t nse
 }
 }  // namespace
 
+// Split-row sums by chunks of 8 column groups for K > 16 (MC_FIXUP_ROWS=0:
+// a warp per column group).
+static bool use_fixup_rows() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_FIXUP_ROWS");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 // Adds the partials of rows longer than one segment (K columns, a multiple of 4).
 static void launch_fixup(cudaStream_t st, const SegPlan &plan, const float *partial, int K, float *out, int ld_out) {
   const int K4 = K / 4;
   const int *sr = plan.split_row.as<int>(), *ss = plan.split_slot.as<int>();
-  if (K4 <= 4)
+  if (K4 <= 4) {
     spmm_fixup_rows_kernel<4><<<grid_for(plan.nsplit * 32, 256, 1 << 20), 256, 0, st>>>(plan.nsplit, sr, ss, partial,
-                                                                                       K, out, ld_out);
-  else if (K4 <= 8)
-    spmm_fixup_rows_kernel<8><<<grid_for(plan.nsplit * 32, 256, 1 << 20), 256, 0, st>>>(plan.nsplit, sr, ss, partial,
-                                                                                       K, out, ld_out);
-  else
+                                                                                       K, out, ld_out, 1);
+  } else if (K4 <= 64 && use_fixup_rows()) {
+    const int nchunk = (K4 + 7) / 8;
+    spmm_fixup_rows_kernel<8><<<grid_for(plan.nsplit * nchunk * 32, 256, 1 << 20), 256, 0, st>>>(
+        plan.nsplit, sr, ss, partial, K, out, ld_out, nchunk);
+  } else {
     spmm_fixup_kernel<<<grid_for(plan.nsplit * K4 * 32, 256), 256, 0, st>>>(plan.nsplit, sr, ss, partial, K, out,
                                                                            ld_out);
+  }
   MC_CHECK_LAUNCH();
 }
 
