@@ -734,6 +734,15 @@ def run_case(args):
                 h.svt_step(prm)
     elif args.case == "serve":
         print(json.dumps(run_serving(mc, args.steps)), flush=True)
+    elif args.case == "panel":
+        # the tensor-core panel kernels on panels larger than L2: Z = X W
+        # (600,000 x 60 times 60 x 60, and 240 x 52) and the Gram X^T X
+        rng = np.random.default_rng(SEED)
+        X = rng.standard_normal((600_000, 60)).astype(np.float32)
+        mc.panel_gemm(X, rng.standard_normal((60, 60)).astype(np.float32), tensor_cores=True)
+        mc.panel_gram(X, X, tensor_cores=True)
+        X = rng.standard_normal((300_000, 240)).astype(np.float32)
+        mc.panel_gemm(X, rng.standard_normal((240, 52)).astype(np.float32), tensor_cores=True)
     elif args.case == "gram":
         X = torch.randn(138_000, 240, device="cuda")
         for _ in range(3):
@@ -804,7 +813,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--case", choices=["spmm", "sddmm", "gram", "serve", "orth", "svt"], default=None,
+    ap.add_argument("--case", choices=["spmm", "sddmm", "gram", "serve", "orth", "svt", "panel"], default=None,
                     help="run one small kernel case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3 or args.steps < 1:

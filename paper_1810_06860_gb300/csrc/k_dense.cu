@@ -660,72 +660,7 @@ chol_inv_blk_kernel(int K, const float *__restrict__ G, int ld, float shift_rel,
     else As[i][j] = i == j ? 1.f : 0.f;  // padding: an identity block, coupled to nothing
   }
   __syncthreads();
-  for (int j0 = 0; j0 < CB_K; j0 += CB_NB) {
-    // (1) the diagonal block: lane a (and a + 16) holds row j0 + a
-    if (wid == 0) {
-      const int a = lane & 15;
-      float r[CB_NB];
-#pragma unroll
-      for (int b = 0; b < CB_NB; ++b) r[b] = b <= a ? As[j0 + a][j0 + b] : 0.f;
-      auto diag_step = [&](const int j) {
-        const float pj = __shfl_sync(full, r[j], j);
-        const bool keep = pj > drop;
-        const float inv = keep ? rsqrtf(pj) : 0.f;
-        if (a > j) r[j] *= inv;
-        const float la = r[j];
-#pragma unroll
-        for (int b = j + 1; b < CB_NB; ++b) {
-          const float lb = __shfl_sync(full, la, b);
-          if (a >= b) r[b] = fmaf(-la, lb, r[b]);
-        }
-        if (lane == 0) {
-          invd[j0 + j] = inv;
-          if (!keep) flags[j0 + j] = 0.f;
-        }
-      };
-#pragma unroll
-      for (int j = 0; j < 8; ++j) diag_step(j);
-#pragma unroll
-      for (int j = 8; j < CB_NB; ++j) diag_step(j);
-      if (lane < CB_NB) {
-#pragma unroll
-        for (int b = 0; b < CB_NB; ++b)
-          if (b <= a) As[j0 + a][j0 + b] = r[b];
-      }
-    }
-    __syncthreads();
-    // (2) the rows below it
-    const int j1 = j0 + CB_NB;
-    if (j1 + tid < CB_K) {
-      const int a = j1 + tid;
-      float r[CB_NB];
-#pragma unroll
-      for (int b = 0; b < CB_NB; ++b) r[b] = As[a][j0 + b];
-#pragma unroll
-      for (int j = 0; j < CB_NB; ++j) {
-        const float l = r[j] * invd[j0 + j];
-        r[j] = l;
-#pragma unroll
-        for (int b = j + 1; b < CB_NB; ++b) r[b] = fmaf(-l, As[j0 + b][j0 + j], r[b]);
-      }
-#pragma unroll
-      for (int b = 0; b < CB_NB; ++b) As[a][j0 + b] = r[b];
-    }
-    __syncthreads();
-    // (3) the trailing matrix
-    if (j1 < CB_K) {
-#pragma unroll 4
-      for (int u = 0; u < 16; ++u) {
-        const int e = tid + CB_THREADS * u, a = e >> 6, b = e & 63;
-        if (b < j1 || b > a) continue;
-        float v = As[a][b];
-#pragma unroll
-        for (int k = 0; k < CB_NB; ++k) v = fmaf(-As[a][j0 + k], As[b][j0 + k], v);
-        As[a][b] = v;
-      }
-    }
-    __syncthreads();
-  }
+  chol64_blocked(As, drop, invd, flags);
   // L^{-1}: thread (c, r) holds entries (4q + r, c); at step k entry (k, c) is
   // final once scaled, and the rows below take its multiple
   const int c = tid >> 2, r = tid & 3, src0 = lane & ~3;

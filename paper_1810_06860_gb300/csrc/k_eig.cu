@@ -1428,8 +1428,9 @@ eig_bisect_kernel(int K, int kw, const float *__restrict__ g_d, const float *__r
 // R^T R.  Equal eigenvalues aside, the columns are already nearly orthogonal,
 // so the Gram is well conditioned; a column whose pivot falls to the noise
 // floor is zeroed.  256 threads: the Gram as eight warp partials (a warp per
-// eighth of the rows, lanes along columns), the Cholesky factor by the
-// block, the solve a thread per row.
+// eighth of the rows, lanes along columns), the Cholesky factor in 16-column
+// blocks (chol64_blocked, the unblocked loop's rounding), the solve a thread
+// per row.
 constexpr int EO_THREADS = 256, EO_KW = 64;
 __global__ void __launch_bounds__(EO_THREADS, 1)
 eig_orth_kernel(int K, int kw, float *__restrict__ Z, int ldz) {
@@ -1439,6 +1440,7 @@ eig_orth_kernel(int K, int kw, float *__restrict__ Z, int ldz) {
   float *P = Zs + (size_t)K * lz;              // 8 x kw x kw warp partials
   float *G = P + (size_t)8 * kw * kw;          // kw x (kw + 1)
   __shared__ float s_drop, s_pivok[EO_KW], rdg[EO_KW];
+  __shared__ float Ls[64][65], linv[64], okf[64];  // the blocked Cholesky's R^T
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int lg = kw + 1;
   for (int f = tid; f < K * kw; f += EO_THREADS) {
@@ -1489,23 +1491,24 @@ eig_orth_kernel(int K, int kw, float *__restrict__ Z, int ldz) {
       s_drop = fmaxf(1e-30f, 1e-12f * mx) + shift;
     }
     __syncthreads();
-    // right-looking Cholesky G = R^T R in place: the strict upper triangle
-    // holds R, its diagonal goes to rdg (G's diagonal is not rewritten, so the
-    // pivot read and the row scaling need no barrier between them); warps
-    // take the rows of the trailing update, lanes its columns
-    for (int j = 0; j < kw; ++j) {
-      const float piv = G[j * lg + j];
-      const bool ok = piv > s_drop;
-      const float inv = ok ? rsqrtf(piv) : 0.f;
-      for (int c = j + 1 + tid; c < kw; c += EO_THREADS) G[j * lg + c] *= inv;
-      if (tid == 0) {
-        rdg[j] = ok ? piv * inv : 0.f;
-        s_pivok[j] = ok ? 1.f : 0.f;
+    // right-looking Cholesky G = R^T R: the strict upper triangle of G takes
+    // R, its diagonal goes to rdg.  The blocked form (kw <= 64) on R^T, padded
+    // with an identity block; its rounding is the unblocked loop's
+    {
+      for (int f = tid; f < 64 * 64; f += EO_THREADS) {
+        const int a = f >> 6, b = f & 63;
+        if (b <= a) Ls[a][b] = a < kw ? G[b * lg + a] : (a == b ? 1.f : 0.f);
       }
+      if (tid < 64) okf[tid] = 1.f;
       __syncthreads();
-      for (int r = j + 1 + wid; r < kw; r += EO_THREADS / 32) {
-        const float grj = G[j * lg + r];
-        for (int c = r + lane; c < kw; c += 32) G[r * lg + c] = fmaf(-grj, G[j * lg + c], G[r * lg + c]);
+      chol64_blocked(Ls, s_drop, linv, okf);
+      for (int f = tid; f < kw * kw; f += EO_THREADS) {
+        const int j = f / kw, c = f % kw;
+        if (c > j) G[j * lg + c] = Ls[c][j];
+      }
+      if (tid < kw) {
+        rdg[tid] = okf[tid] != 0.f ? Ls[tid][tid] * linv[tid] : 0.f;
+        s_pivok[tid] = okf[tid];
       }
       __syncthreads();
     }

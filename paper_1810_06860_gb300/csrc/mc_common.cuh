@@ -266,4 +266,88 @@ size_t eig_work_bytes(int K, int kw);
 void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *lam, float *W, int ld_w,
               void *work);
 
+
+// Blocked right-looking Cholesky of the lower triangle of a 64 x 64 matrix in
+// shared memory (As[a][b], b <= a; 256 threads, all of which call it).  Every
+// entry takes its updates one fused multiply-add at a time in pivot order,
+// as the unblocked right-looking loop does, so the result is that loop's:
+// on return As holds L below the diagonal (column j scaled by 1/sqrt of the
+// pivot), the diagonal keeps the pivots A[j][j] before scaling, invd[j] =
+// 1/sqrt(pivot) (0 for a pivot at or below drop) and flags[j] = 0 for a
+// dropped pivot (otherwise untouched).  In 16-column blocks: (1) one warp
+// factors the diagonal block, lane a holding row a in registers and each
+// step's column passed by shuffles; (2) a thread per row below solves it
+// against the block; (3) a thread per entry applies the block's rank-16
+// update to the trailing matrix; three block barriers per block.
+__device__ __forceinline__ void chol64_blocked(float (*As)[65], float drop, float *invd, float *flags) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned full = 0xffffffffu;
+  for (int j0 = 0; j0 < 64; j0 += 16) {
+    // (1) the diagonal block: lane a (and a + 16) holds row j0 + a
+    if (wid == 0) {
+      const int a = lane & 15;
+      float r[16];
+#pragma unroll
+      for (int b = 0; b < 16; ++b) r[b] = b <= a ? As[j0 + a][j0 + b] : 0.f;
+      auto diag_step = [&](const int j) {
+        const float pj = __shfl_sync(full, r[j], j);
+        const bool keep = pj > drop;
+        const float inv = keep ? rsqrtf(pj) : 0.f;
+        if (a > j) r[j] *= inv;
+        const float la = r[j];
+#pragma unroll
+        for (int b = j + 1; b < 16; ++b) {
+          const float lb = __shfl_sync(full, la, b);
+          if (a >= b) r[b] = fmaf(-la, lb, r[b]);
+        }
+        if (lane == 0) {
+          invd[j0 + j] = inv;
+          if (!keep) flags[j0 + j] = 0.f;
+        }
+      };
+#pragma unroll
+      for (int j = 0; j < 8; ++j) diag_step(j);
+#pragma unroll
+      for (int j = 8; j < 16; ++j) diag_step(j);
+      if (lane < 16) {
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+          if (b <= a) As[j0 + a][j0 + b] = r[b];
+      }
+    }
+    __syncthreads();
+    // (2) the rows below it
+    const int j1 = j0 + 16;
+    if (j1 + tid < 64) {
+      const int a = j1 + tid;
+      float r[16];
+#pragma unroll
+      for (int b = 0; b < 16; ++b) r[b] = As[a][j0 + b];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float l = r[j] * invd[j0 + j];
+        r[j] = l;
+#pragma unroll
+        for (int b = j + 1; b < 16; ++b) r[b] = fmaf(-l, As[j0 + b][j0 + j], r[b]);
+      }
+#pragma unroll
+      for (int b = 0; b < 16; ++b) As[a][j0 + b] = r[b];
+    }
+    __syncthreads();
+    // (3) the trailing matrix
+    if (j1 < 64) {
+#pragma unroll 4
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * u, a = e >> 6, b = e & 63;
+        if (b < j1 || b > a) continue;
+        float v = As[a][b];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v = fmaf(-As[a][j0 + k], As[b][j0 + k], v);
+        As[a][b] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace mc

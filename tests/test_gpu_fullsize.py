@@ -101,12 +101,13 @@ def test_svt_window_matches_stored_oracle(mc, rating, stored):
     rmse = {int(k): v for k, v in stored["heldout_rmse"].items()}
     assert ref[-1]["r"] >= 40 and rmse
     prm = mc.params(**stored["params"])
-    worst = 0.0
+    worst = worst_err = 0.0
     with mc.Handle.from_observed(o) as h:
         for b in ref:
             a = h.svt_step(prm)
             assert a["i"] == b["i"]
             assert (a["k"], a["r"], a["p"]) == (b["k"], b["r"], b["p"]), (a, b)
+            worst_err = max(worst_err, abs(a["err"] - b["err"]) / b["err"])
             assert abs(a["err"] - b["err"]) <= 1e-4 * b["err"], (a, b)
             if b["i"] == 1:
                 assert a["c"] == b["c"]
@@ -114,7 +115,8 @@ def test_svt_window_matches_stored_oracle(mc, rating, stored):
                 d = abs(_heldout_rmse(h, o) - rmse[b["i"]])
                 worst = max(worst, d)
                 assert d <= 1e-3, (b["i"], d)
-    print(f"largest held-out RMSE difference from the oracle: {worst:.2e}")
+    print(f"largest held-out RMSE difference from the oracle: {worst:.2e}; "
+          f"largest relative error difference on Phi: {worst_err:.2e}")
 
 
 def test_svt_window_mixed_form_heldout_rmse(mc, rating, stored):
