@@ -534,8 +534,9 @@ def run_ours(args, rank, world, local):
             "timing_ms": {k: round(v["ms"], 3) for k, v in tm_all.items()},
             "kernel_ms_per_step": round(sum(v["ms"] for v in tm_all.values()) / args.steps, 3),
             "timing_note": "per-class CUDA-event ms over the steps after the timed ones (same count); "
-                           "kernel_ms_per_step is their sum per step, beside ms_per_step (events around every "
-                           "launch add about 5 %; the rest of the gap is host time between kernels)"}
+                           "kernel_ms_per_step is their sum per step, beside ms_per_step: events around every "
+                           "launch serialise the classes and add their own cost, so it bounds the kernel time "
+                           "from above"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
