@@ -717,27 +717,32 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
 // CTA covers a range of rows and writes one partial K1_p x K2_p tile; a
 // fixed-order reduction adds the partials.
 //
-// Warp-specialised, 384 threads:
-//   warp 0, lane 0   TMA producer: the stage's 32-column boxes of X1 (and of
-//                    X2 unless it is X1) once the splitters released the stage;
-//   warps 4..11      split every value into TF32 hi and lo (rounded to nearest)
-//                    and write both transposed, then release the raw stage
-//                    and hand the split stage to the issuer;
+// Warp-specialised, 384 threads, two rings in shared memory:
+//   warp 0, lane 0   TMA producer: raw stages of 32 nsub rows (nsub = 1, 2
+//                    or 4), the 32-column boxes of X1 (and of X2 unless it
+//                    is X1), once the splitters released the raw stage (tall
+//                    boxes: fewer, larger copies);
+//   warps 4..11      split each 32-row part of a raw stage into TF32 hi and
+//                    lo (rounded to nearest) and write both transposed into
+//                    a split stage, handing it to the issuer; the raw stage
+//                    is released after its last part;
 //   warp 1, lane 0   MMA issuer: hi*hi + hi*lo + lo*hi for every 8-row step
-//                    into one accumulator per 128 columns of X1, releasing the
-//                    split stage by a commit;
+//                    into one accumulator per 128 columns of X1 (for the Gram
+//                    of 33..64 columns one MMA, hi^T [hi | lo], see below),
+//                    releasing the split stage by a commit;
 //   warps 8..11      after the last stage, read the accumulators (tcgen05.ld)
 //                    and write the partial tile.
-// Every wait is bounded; an expiry ends every role, each drains its own
-// copies or MMAs, and the error code goes to err.
+// The MMAs take the 32-row parts in row order.  Every wait is bounded; an
+// expiry ends every role, each drains its own copies or MMAs, and the error
+// code goes to err.
 constexpr int TT_THREADS = 384, TT_KT = 32, TT_MAXST = 6;
 constexpr int TT_BOX = TT_KT * 32 * 4;  // 32 rows x 32 columns: 4 KiB
 
 __global__ void __launch_bounds__(TT_THREADS, 1)
 gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, int same,
-                     int64_t R, int nbA, int nbB, int Np, int mt, uint32_t tmem_cols, int nst, int64_t rows_per_cta,
-                     float *__restrict__ partial, int K1p, int K2p, int *__restrict__ err,
-                     const int *__restrict__ skip) {
+                     int sym, int64_t R, int nbA, int nbB, int Np, int mt, uint32_t tmem_cols, int nsub, int nr,
+                     int ns, int64_t rows_per_cta, float *__restrict__ partial, int K1p, int K2p,
+                     int *__restrict__ err, const int *__restrict__ skip) {
   extern __shared__ __align__(1024) uint8_t tt_raw_smem[];
   __shared__ __align__(8) uint64_t full_bar[TT_MAXST], rawfree_bar[TT_MAXST], split_bar[TT_MAXST],
       splitfree_bar[TT_MAXST];
@@ -747,23 +752,27 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
   if (skip && *skip) return;  // a pass the previous one made unnecessary
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tt_raw_smem) + 1023) & ~uintptr_t(1023));
   const int nbr = nbA + (same ? 0 : nbB);                  // raw boxes per stage
-  const size_t raw_bytes = (size_t)nbr * TT_BOX;
+  const int rb = TT_KT * nsub;                             // rows per raw stage
+  const size_t box_bytes = (size_t)rb * 128;               // one 32-column box of a raw stage
+  const size_t raw_bytes = (size_t)nbr * box_bytes;
   const size_t spl_bytes = (size_t)(4 * mt + (same ? 0 : nbB)) * TT_BOX;  // one of hi / lo
-  const size_t stage_bytes = raw_bytes + 2 * spl_bytes;
-  auto raw = [&](int s) { return base + (size_t)s * stage_bytes; };
-  auto hi = [&](int s) { return base + (size_t)s * stage_bytes + raw_bytes; };
-  auto lo = [&](int s) { return base + (size_t)s * stage_bytes + raw_bytes + spl_bytes; };
+  auto raw = [&](int s) { return base + (size_t)s * raw_bytes; };
+  auto hi = [&](int s) { return base + (size_t)nr * raw_bytes + (size_t)s * 2 * spl_bytes; };
+  auto lo = [&](int s) { return base + (size_t)nr * raw_bytes + (size_t)s * 2 * spl_bytes + spl_bytes; };
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t r0 = blockIdx.x * rows_per_cta;
   const int64_t r1 = min(R, r0 + rows_per_cta);
-  const int S = r1 > r0 ? static_cast<int>((r1 - r0 + TT_KT - 1) / TT_KT) : 0;
+  const int S = r1 > r0 ? static_cast<int>((r1 - r0 + TT_KT - 1) / TT_KT) : 0;  // 32-row parts
+  const int SR = (S + nsub - 1) / nsub;                                           // raw stages
   volatile int *vfail = &s_fail;
   const unsigned fullm = 0xffffffffu;
 
   if (tid == 0) {
-    for (int s = 0; s < nst; ++s) {
+    for (int s = 0; s < nr; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&rawfree_bar[s], 8);  // one arrival per split warp
+    }
+    for (int s = 0; s < ns; ++s) {
       mbar_init(&split_bar[s], 8);
       mbar_init(&splitfree_bar[s], 1);  // MMA commit
     }
@@ -788,33 +797,33 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
     // ---- TMA producer ----
     if (lane == 0) {
       int issued = 0, s = 0;
-      uint32_t ph = 0;  // parity of stage s's current use
+      uint32_t ph = 0;  // parity of raw stage s's current use
       int y = static_cast<int>(r0);
-      for (int g = 0; g < S; ++g, y += TT_KT) {
+      for (int g = 0; g < SR; ++g, y += rb) {
         if (failed(vfail)) break;
-        if (g >= nst && !mbar_wait(&rawfree_bar[s], ph ^ 1u)) {
+        if (g >= nr && !mbar_wait(&rawfree_bar[s], ph ^ 1u)) {
           atomicOr(&s_fail, 1);
           break;
         }
         mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(raw_bytes));
-        for (int j = 0; j < nbA; ++j) tma_load_2d(raw(s) + j * TT_BOX, &amap, 32 * j, y, &full_bar[s]);
+        for (int j = 0; j < nbA; ++j) tma_load_2d(raw(s) + j * box_bytes, &amap, 32 * j, y, &full_bar[s]);
         if (!same)
-          for (int j = 0; j < nbB; ++j) tma_load_2d(raw(s) + (nbA + j) * TT_BOX, &bmap, 32 * j, y, &full_bar[s]);
+          for (int j = 0; j < nbB; ++j) tma_load_2d(raw(s) + (nbA + j) * box_bytes, &bmap, 32 * j, y, &full_bar[s]);
         issued = g + 1;
-        if (++s == nst) {
+        if (++s == nr) {
           s = 0;
           ph ^= 1u;
         }
       }
-      for (int g = max(0, issued - nst); g < issued; ++g) mbar_wait(&full_bar[g % nst], (g / nst) & 1);
+      for (int g = max(0, issued - nr); g < issued; ++g) mbar_wait(&full_bar[g % nr], (g / nr) & 1);
     }
   } else if (wid == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
       // one thread issues every MMA: incremental stage and phase, descriptors
       // moved by adding address units (16 bytes)
-      const uint32_t idesc = idesc_tf32(128, Np);
-      const uint64_t sstep = static_cast<uint64_t>(stage_bytes) >> 4;
+      const uint32_t idesc = idesc_tf32(128, Np), idesc_sym = idesc_tf32(128, 128);
+      const uint64_t sstep = static_cast<uint64_t>(2 * spl_bytes) >> 4;
       const uint64_t dh0 = smem_desc(smem_u32(hi(0))), dl0 = smem_desc(smem_u32(lo(0)));
       const uint64_t boff = same ? 0 : static_cast<uint64_t>(aboxes * TT_BOX) >> 4;
       int committed = -1, ncommit = 0, s = 0;
@@ -827,7 +836,14 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
         }
         tc_fence_after();
         const uint64_t ah = dh0 + s * sstep, al = dl0 + s * sstep, bh = ah + boff, bl = al + boff;
-        if (mt == 1) {
+        if (sym) {
+          // the Gram of at most 64 columns: the stage holds [hi | lo] as 128
+          // operand rows, so one MMA per 8-row step gives hi^T hi (columns
+          // 0..63) and hi^T lo (64..127); lo^T hi is the latter's transpose
+#pragma unroll
+          for (int ks = 0; ks < TT_KT / 8; ++ks)
+            mma_tf32(tmem, ah + 2 * ks, ah + 2 * ks, idesc_sym, (g > 0 || ks > 0) ? 1u : 0u);
+        } else if (mt == 1) {
 #pragma unroll
           for (int ks = 0; ks < TT_KT / 8; ++ks) {
             const uint32_t acc0 = (g > 0 || ks > 0) ? 1u : 0u;
@@ -852,7 +868,7 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
         committed = s;
         committed_ph = ph;
         ++ncommit;
-        if (++s == nst) {
+        if (++s == ns) {
           s = 0;
           ph ^= 1u;
         }
@@ -863,29 +879,31 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
   } else if (wid >= 4) {
     // ---- transpose and split ----
     const int st = tid - 128;
-    int s = 0;
-    uint32_t ph = 0;
-    for (int g = 0; g < S; ++g, s = s + 1 == nst ? 0 : s + 1, ph ^= s == 0 ? 1u : 0u) {
+    int sr = 0, ss = 0, sub = 0;
+    uint32_t phr = 0, phs = 0;
+    for (int g = 0; g < S; ++g) {
       if (__any_sync(fullm, failed(vfail))) break;
-      bool ok = mbar_wait(&full_bar[s], ph);
-      if (ok && g >= nst) ok = mbar_wait(&splitfree_bar[s], ph ^ 1u);
+      bool ok = sub != 0 || mbar_wait(&full_bar[sr], phr);
+      if (ok && g >= ns) ok = mbar_wait(&splitfree_bar[ss], phs ^ 1u);
       if (!__all_sync(fullm, ok)) {
         atomicOr(&s_fail, 2);
         break;
       }
-      // TMA box j holds element (row r, column 32 j + cc) at
-      //   j * 1024 + r * 32 + (((cc / 4) ^ (r % 8)) * 4) + cc % 4   (floats);
-      // the K-major operand stores global column c at
-      //   (c / 8) * 256 + (c % 8) * 32 + (((r / 4) ^ (c % 8)) * 4) + r % 4,
-      // with B's columns after A's 4 mt boxes.  A warp takes one 4-column
-      // group of a box across its 32 rows (lane = row): conflict-free.
-      const float4 *src = reinterpret_cast<const float4 *>(raw(s));
-      float *dh = reinterpret_cast<float *>(hi(s)), *dl = reinterpret_cast<float *>(lo(s));
+      // raw box j holds element (row r of the stage, column 32 j + cc) at
+      //   j * 32 rb + r * 32 + (((cc / 4) ^ (r % 8)) * 4) + cc % 4   (floats);
+      // part sub takes rows r = 32 sub + rr, and the K-major operand stores
+      // global column c at
+      //   (c / 8) * 256 + (c % 8) * 32 + (((rr / 4) ^ (c % 8)) * 4) + rr % 4,
+      // with B's columns after A's 4 mt boxes (for the folded Gram, lo at
+      // column c + 64 of the same operand).  A warp takes one 4-column group
+      // of a box across its 32 rows (lane = row): conflict-free.
+      const float4 *src = reinterpret_cast<const float4 *>(raw(sr)) + sub * TT_KT * 8;
+      float *dh = reinterpret_cast<float *>(hi(ss)), *dl = reinterpret_cast<float *>(lo(ss));
       for (int q = st; q < nbr * 256; q += 256) {
         const int box = q >> 8, k4 = (q >> 5) & 7, r = q & 31;
         const int obox = box < nbA ? box : aboxes + (box - nbA);
         const int c0 = obox * 32 + k4 * 4;
-        const float4 v = src[box * 256 + r * 8 + (k4 ^ (r & 7))];
+        const float4 v = src[box * (rb * 8) + r * 8 + (k4 ^ (r & 7))];
         const float vals[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -894,14 +912,29 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
           float h, l;
           tf32_split(vals[u], h, l);
           dh[off] = h;
-          dl[off] = l;
+          if (sym) dh[off + 2048] = l;  // column c + 64 of the same operand
+          else dl[off] = l;
         }
       }
       fence_proxy_async();
       __syncwarp();
+      const bool last_part = sub == nsub - 1;
       if (lane == 0) {
-        mbar_arrive(&rawfree_bar[s]);
-        mbar_arrive(&split_bar[s]);
+        mbar_arrive(&split_bar[ss]);
+        if (last_part) mbar_arrive(&rawfree_bar[sr]);
+      }
+      if (++ss == ns) {
+        ss = 0;
+        phs ^= 1u;
+      }
+      if (last_part) {
+        sub = 0;
+        if (++sr == nr) {
+          sr = 0;
+          phr ^= 1u;
+        }
+      } else {
+        ++sub;
       }
     }
   }
@@ -920,7 +953,37 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
     }
     tc_fence_after();
     float *out = partial + (size_t)blockIdx.x * K1p * K2p;
-    for (int t = 0; t < mt; ++t) {
+    if (sym) {
+      // G = hi^T hi + C + C^T with C = hi^T lo: rows 0..63 (warps 8, 9) put C
+      // in shared memory (the stages are idle now), then every entry adds its
+      // transpose
+      float(*Ct)[65] = reinterpret_cast<float(*)[65]>(base);
+      const int i = 32 * ew + lane;
+      if (ew < 2) {
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          float v[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] = 0.f;
+          if (ok) tmem_ld16(tmem + (static_cast<uint32_t>(32 * ew) << 16) + static_cast<uint32_t>(64 + c0), v);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) Ct[i][c0 + k] = v[k];
+        }
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          float a[16], b[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) a[k] = b[k] = 0.f;
+          if (ok) {
+            tmem_ld16(tmem + (static_cast<uint32_t>(32 * ew) << 16) + static_cast<uint32_t>(c0), a);
+            tmem_ld16(tmem + (static_cast<uint32_t>(32 * ew) << 16) + static_cast<uint32_t>(64 + c0), b);
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (c0 + k < K2p) out[(size_t)i * K2p + c0 + k] = (a[k] + b[k]) + Ct[c0 + k][i];
+        }
+      }
+    }
+    for (int t = 0; t < (sym ? 0 : mt); ++t) {
       const int i = t * 128 + 32 * ew + lane;
       for (int c0 = 0; c0 < Np; c0 += 16) {
         float v[16];
@@ -1048,11 +1111,13 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
 namespace {
 constexpr size_t TT_SMEM = 226 * 1024;
 struct TtPlan {
-  int K1p, K2p, nbA, nbB, Np, mt, nst, nsplit;
+  int K1p, K2p, nbA, nbB, Np, mt, nsub, nr, ns, nsplit;
   uint32_t cols;
   size_t smem;
   int64_t rows_per;
 };
+// Raw stages of 32 nsub rows (the tallest copies that leave two raw and two
+// split stages), two raw stages, and up to four split stages.
 TtPlan tt_plan(int64_t R, int K1, int K2, bool same) {
   TtPlan p{};
   p.K1p = static_cast<int>(round_up(K1, 32));
@@ -1061,10 +1126,21 @@ TtPlan tt_plan(int64_t R, int K1, int K2, bool same) {
   p.nbB = same ? 0 : p.K2p / 32;
   p.Np = static_cast<int>(round_up(K2, 16));
   p.mt = p.K1p > 128 ? 2 : 1;
-  const size_t raw = (size_t)(p.nbA + p.nbB) * TT_BOX, spl = (size_t)(4 * p.mt + p.nbB) * TT_BOX;
-  const size_t stage = raw + 2 * spl;
-  p.nst = static_cast<int>(std::min<size_t>(TT_MAXST, (TT_SMEM - 1024) / stage));
-  p.smem = (size_t)p.nst * stage + 1024;
+  const size_t spl = (size_t)(4 * p.mt + p.nbB) * TT_BOX;
+  p.nsub = 0;
+  for (int nsub : {4, 2, 1}) {
+    const size_t raw = (size_t)(p.nbA + p.nbB) * TT_BOX * nsub;
+    for (int ns : {4, 3, 2}) {
+      if (2 * raw + (size_t)ns * 2 * spl + 1024 <= TT_SMEM) {
+        p.nsub = nsub;
+        p.nr = 2;
+        p.ns = ns;
+        p.smem = 2 * raw + (size_t)ns * 2 * spl + 1024;
+        break;
+      }
+    }
+    if (p.nsub) break;
+  }
   p.cols = 32;
   while (p.cols < static_cast<uint32_t>(p.mt * p.Np)) p.cols <<= 1;
   p.nsplit = tc_nsplit(R);
@@ -1072,11 +1148,11 @@ TtPlan tt_plan(int64_t R, int K1, int K2, bool same) {
   p.nsplit = static_cast<int>((R + p.rows_per - 1) / p.rows_per);
   return p;
 }
-CUtensorMap tt_map(const float *X, int64_t R, int K, int ld) {
+CUtensorMap tt_map(const float *X, int64_t R, int K, int ld, int rows) {
   CUtensorMap map;
   const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(R)};
   const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
-  const cuuint32_t box[2] = {32, static_cast<cuuint32_t>(TT_KT)};
+  const cuuint32_t box[2] = {32, static_cast<cuuint32_t>(rows)};
   const cuuint32_t estride[2] = {1, 1};
   const CUresult cr = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), gdim, gstride, box,
                                   estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1086,11 +1162,21 @@ CUtensorMap tt_map(const float *X, int64_t R, int K, int ld) {
 }
 }  // namespace
 
+// Grams of 33..64 columns with the cross terms folded into one MMA per step
+// (MC_TN_SYM=0: three MMAs per step, hi*hi + hi*lo + lo*hi in one accumulator).
+bool use_tn_sym() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_TN_SYM");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 bool gemm_tn_tc_supported(int64_t R, int K1, int K2, const void *X1, int ld1, const void *X2, int ld2) {
   if (R < 1 || R >= (int64_t(1) << 31) || K1 < 1 || K2 < 1 || K1 > 256 || K2 > 256) return false;
   if (ld1 < K1 || ld2 < K2 || ld1 % 4 || ld2 % 4) return false;
   if (((reinterpret_cast<uintptr_t>(X1) | reinterpret_cast<uintptr_t>(X2)) & 15u) != 0) return false;
-  return tt_plan(R, K1, K2, X1 == X2 && ld1 == ld2 && K1 == K2).nst >= 2;
+  return tt_plan(R, K1, K2, X1 == X2 && ld1 == ld2 && K1 == K2).nsub > 0;
 }
 
 size_t gemm_tn_tc_scratch_floats(int64_t R, int K1, int K2) {
@@ -1103,12 +1189,14 @@ void gemm_tn_tc(cudaStream_t st, int64_t R, int K1, int K2, const float *X1, int
   MC_REQUIRE(gemm_tn_tc_supported(R, K1, K2, X1, ld1, X2, ld2), "gemm_tn_tc: shape or alignment not supported");
   const bool same = X1 == X2 && ld1 == ld2 && K1 == K2;
   const TtPlan p = tt_plan(R, K1, K2, same);
-  const CUtensorMap amap = tt_map(X1, R, K1, ld1);
-  const CUtensorMap bmap = same ? amap : tt_map(X2, R, K2, ld2);
+  const CUtensorMap amap = tt_map(X1, R, K1, ld1, TT_KT * p.nsub);
+  const CUtensorMap bmap = same ? amap : tt_map(X2, R, K2, ld2, TT_KT * p.nsub);
   MC_CUDA(cudaFuncSetAttribute(gemm_tn_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM));
-  gemm_tn_tc_ws_kernel<<<p.nsplit, TT_THREADS, p.smem, st>>>(amap, bmap, same ? 1 : 0, R, p.nbA, p.nbB, p.Np, p.mt,
-                                                              p.cols, p.nst, p.rows_per, partial, p.K1p, p.K2p,
-                                                              err, skip);
+  // the Gram of 33..64 columns in one MMA per step (hi^T [hi | lo])
+  const bool sym = same && p.nbA == 2 && p.mt == 1 && use_tn_sym();
+  gemm_tn_tc_ws_kernel<<<p.nsplit, TT_THREADS, p.smem, st>>>(amap, bmap, same ? 1 : 0, sym ? 1 : 0, R, p.nbA, p.nbB,
+                                                              p.Np, p.mt, sym ? 128u : p.cols, p.nsub, p.nr, p.ns,
+                                                              p.rows_per, partial, p.K1p, p.K2p, err, skip);
   MC_CHECK_LAUNCH();
   gemm_tn_reduce_partials(st, K1, K2, p.nsplit, partial, p.K1p, p.K2p, C, ld_c, skip);
 }
