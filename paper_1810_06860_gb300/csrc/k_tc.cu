@@ -410,7 +410,7 @@ __device__ __forceinline__ bool failed(const volatile int *f) { return *f != 0; 
 
 __global__ void __launch_bounds__(NW_THREADS, 1)
 gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap zmap, int zmode,
-                     int ebuf, int64_t R, int K, int N, int Kp, int Np,
+                     int ebuf, int cat, int64_t R, int K, int N, int Kp, int Np,
                      uint32_t tmem_cols, int nst, const float *__restrict__ W, int ld_w,
                      const float *__restrict__ colscale, float alpha, float beta, float *__restrict__ Z, int ld_z,
                      int *__restrict__ err, const int *__restrict__ copy_if, int ld_x, const float *__restrict__ Xp) {
@@ -471,8 +471,10 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
   }
   // W^T (N_p x K_p, K-major, 128-byte swizzle) as hi and lo: element (n, k) of
   // column block kc at kc * N_p * 128 + (n / 8) * 1024 + (n % 8) * 128 +
-  // (((k % 32) / 4) ^ (n % 8)) * 16 + (k % 4) * 4.  Eight loads per thread are
-  // in flight before their values are split and stored.
+  // (((k % 32) / 4) ^ (n % 8)) * 16 + (k % 4) * 4 of its part; with cat the
+  // parts interleave by column block, [hi | lo] as 2 N_p operand rows per
+  // block (one MMA then takes X_hi against both).  Eight loads per thread
+  // are in flight before their values are split and stored.
   for (int e0 = tid; e0 < Kp * Np; e0 += 8 * NW_THREADS) {
     float w[8];
 #pragma unroll
@@ -487,10 +489,10 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
       const int kc = k / NT_KC, kl = k % NT_KC;
       float h, lw;
       tf32_split(w[u], h, lw);
-      const size_t off =
-          (size_t)kc * Np * 128 + (n >> 3) * 1024 + (n & 7) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
+      const size_t off = (size_t)kc * Np * 128 * (cat ? 2 : 1) + (n >> 3) * 1024 + (n & 7) * 128 +
+                         (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
       *reinterpret_cast<float *>(whi + off) = h;
-      *reinterpret_cast<float *>(wlo + off) = lw;
+      *reinterpret_cast<float *>((cat ? whi + (size_t)Np * 128 : wlo) + off) = lw;
     }
   }
   fence_proxy_async();
@@ -532,8 +534,8 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
       // A single thread issues every MMA, so the loop keeps its stage, phase,
       // chunk and tile counters incrementally and moves descriptors by adding
       // address units (16 bytes) instead of rebuilding them.
-      const uint32_t idesc = idesc_tf32(NT_BM, Np);
-      const uint64_t wstep = static_cast<uint64_t>(Np) * 128 >> 4;       // one 32-row block of W^T
+      const uint32_t idesc = idesc_tf32(NT_BM, Np), idesc2 = idesc_tf32(NT_BM, 2 * Np);
+      const uint64_t wstep = static_cast<uint64_t>(Np) * 128 * (cat ? 2 : 1) >> 4;  // one 32-row block of W^T
       const uint64_t xstep = static_cast<uint64_t>(2 * NT_BOX_BYTES) >> 4;  // one (hi, lo) stage
       const uint64_t dwh = smem_desc(smem_u32(whi)), dwl = smem_desc(smem_u32(wlo)), dx = smem_desc(smem_u32(stg));
       int committed = -1;
@@ -552,15 +554,26 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + static_cast<uint32_t>(a * Np);
+        const uint32_t d = tmem + static_cast<uint32_t>(a * Np * (cat ? 2 : 1));
         const uint64_t ah = dx + s * xstep, al = ah + (NT_BOX_BYTES >> 4);
         const uint64_t bh = dwh + kc * wstep, bl = dwl + kc * wstep;
+        if (cat) {
+          // X_hi [W_hi | W_lo] into accumulator columns [0, Np) and [Np, 2 Np),
+          // X_lo W_hi into [0, Np); the epilogue adds the two halves
 #pragma unroll
-        for (int ks = 0; ks < NT_KC / 8; ++ks) {
-          const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(d, ah + 2 * ks, bh + 2 * ks, idesc, acc0);  // 8 columns = 32 bytes further
-          mma_tf32(d, ah + 2 * ks, bl + 2 * ks, idesc, 1u);
-          mma_tf32(d, al + 2 * ks, bh + 2 * ks, idesc, 1u);
+          for (int ks = 0; ks < NT_KC / 8; ++ks) {
+            const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32(d, ah + 2 * ks, bh + 2 * ks, idesc2, acc0);
+            mma_tf32(d, al + 2 * ks, bh + 2 * ks, idesc, 1u);
+          }
+        } else {
+#pragma unroll
+          for (int ks = 0; ks < NT_KC / 8; ++ks) {
+            const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32(d, ah + 2 * ks, bh + 2 * ks, idesc, acc0);  // 8 columns = 32 bytes further
+            mma_tf32(d, ah + 2 * ks, bl + 2 * ks, idesc, 1u);
+            mma_tf32(d, al + 2 * ks, bh + 2 * ks, idesc, 1u);
+          }
         }
         mma_commit(&empty_bar[s]);
         if (kc == kchunks - 1) mma_commit(&accf_bar[a]);
@@ -638,7 +651,15 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
         }
         for (int c = 0; c < 32 && c0 + c < N; c += 16) {
           float v[16];
-          tmem_ld16(tmem + (static_cast<uint32_t>(32 * ew) << 16) + static_cast<uint32_t>(a * Np + c0 + c), v);
+          const uint32_t ta = tmem + (static_cast<uint32_t>(32 * ew) << 16) +
+                              static_cast<uint32_t>(a * Np * (cat ? 2 : 1) + c0 + c);
+          tmem_ld16(ta, v);
+          if (cat) {
+            float v2[16];
+            tmem_ld16(ta + static_cast<uint32_t>(Np), v2);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] += v2[k];
+          }
           if (zmode != 0) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -899,6 +920,7 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
       // of a box across its 32 rows (lane = row): conflict-free.
       const float4 *src = reinterpret_cast<const float4 *>(raw(sr)) + sub * TT_KT * 8;
       float *dh = reinterpret_cast<float *>(hi(ss)), *dl = reinterpret_cast<float *>(lo(ss));
+#pragma unroll 2
       for (int q = st; q < nbr * 256; q += 256) {
         const int box = q >> 8, k4 = (q >> 5) & 7, r = q & 31;
         const int obox = box < nbA ? box : aboxes + (box - nbA);
@@ -1056,6 +1078,16 @@ NtPlan nt_plan(int K, int N) {
 }
 }  // namespace
 
+// X_hi against [W_hi | W_lo] in one MMA per 8-column step for N <= 128
+// (MC_NN_CAT=0: three MMAs per step into one accumulator).
+bool use_nn_cat() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_NN_CAT");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 bool gemm_nn_tc_supported(int64_t R, int K, int N, const void *X, int ld_x) {
   if (R < 1 || R >= (int64_t(1) << 31) || K < 1 || N < 1 || N > 256 || ld_x < K || ld_x % 4 != 0) return false;
   if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return false;
@@ -1101,7 +1133,10 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
   const int grid = static_cast<int>(std::min<int64_t>(ntiles, sms));
   MC_CUDA(cudaFuncSetAttribute(gemm_nn_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)NT_SMEM_LIMIT));
-  gemm_nn_tc_ws_kernel<<<grid, NW_THREADS, p.smem, st>>>(map, zmap, zmode, p.ebuf, R, K, N, p.Kp, p.Np, p.cols,
+  const int cat = p.Np <= 128 && use_nn_cat() ? 1 : 0;
+  uint32_t cols = p.cols;
+  while (cat && cols < static_cast<uint32_t>(4 * p.Np)) cols <<= 1;
+  gemm_nn_tc_ws_kernel<<<grid, NW_THREADS, p.smem, st>>>(map, zmap, zmode, p.ebuf, cat, R, K, N, p.Kp, p.Np, cols,
                                                           p.nst, W, ld_w, colscale, alpha, beta, Z, ld_z, err,
                                                           copy_if, ld_x, X);
   MC_CHECK_LAUNCH();
