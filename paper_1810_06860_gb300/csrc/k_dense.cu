@@ -1287,8 +1287,7 @@ static void launch_tn_small(cudaStream_t st, int64_t R, int K1, int K2, const fl
   const size_t smem = TnSmall<T>::smem_bytes(same && pl.tiles_i * pl.tiles_j == 1);
   // the attribute is per kernel and process-wide: always set the largest size
   // any call needs, so concurrent callers on other threads never lower it
-  MC_CUDA(cudaFuncSetAttribute(gemm_tn_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)TnSmall<T>::smem_bytes(false)));
+  smem_attr(gemm_tn_small_kernel<T>, (int)TnSmall<T>::smem_bytes(false));
   dim3 grid((unsigned)pl.nsplit, (unsigned)(pl.tiles_i * pl.tiles_j));
   gemm_tn_small_kernel<T><<<grid, 256, smem, st>>>(R, K1, K2, X, ld_x, Y, ld_y, pl.rps, symg ? 1 : 0, same ? 1 : 0,
                                                    partial, pl.tiles_j, pl.K1p, pl.K2p, skip);
@@ -1358,8 +1357,7 @@ void gemm_nn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, in
     if (K2 <= 4) MC_NN_NARROW(4);
     else if (K2 <= 8) MC_NN_NARROW(8);
     else {
-      MC_CUDA(cudaFuncSetAttribute(gemm_nn_narrow_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(float) * 1024 * 16)));
+      smem_attr(gemm_nn_narrow_kernel<16>, (int)(sizeof(float) * 1024 * 16));
       MC_NN_NARROW(16);
     }
 #undef MC_NN_NARROW
@@ -1376,8 +1374,7 @@ void gemm_nn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, in
     const int64_t per = std::max<int64_t>(1, (nch + want - 1) / want);
     const dim3 grid(static_cast<unsigned>((nch + per - 1) / per), static_cast<unsigned>(tiles));
 #define MC_NN_SMALL(KM)                                                                                              \
-  MC_CUDA(cudaFuncSetAttribute(gemm_nn_small_kernel<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
-                               (int)NnSmall<KM>::smem));                                                             \
+  smem_attr(gemm_nn_small_kernel<KM>, (int)NnSmall<KM>::smem);                                                \
   gemm_nn_small_kernel<KM><<<grid, 256, NnSmall<KM>::smem, st>>>(R, K1, K2, X, ld_x, W, ld_w, colscale, alpha, beta, \
                                                                  Z, ld_z, per, copy_if)
     MC_NN_SMALL(64);
@@ -1423,7 +1420,7 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
     const int ls = (K % 2 == 0) ? K + 1 : K;
     const size_t need = sizeof(float) * (2 * (size_t)K * ls + K);
     constexpr size_t kMax = sizeof(float) * (2 * 128 * 129 + 128);  // K = 128; fixed for concurrent callers
-    MC_CUDA(cudaFuncSetAttribute(chol_inv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax));
+    smem_attr(chol_inv_small_kernel, (int)kMax);
     const int threads = K <= 32 ? 256 : (K <= 64 ? 512 : 1024);
     chol_inv_small_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip,
                                                     skip3_tol());
@@ -1435,7 +1432,7 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
   MC_REQUIRE(base <= 220 * 1024, "chol_inv: block too wide for shared memory");
   const bool x_sm = base + sizeof(float) * (size_t)K * K <= 220 * 1024;
   const size_t need = x_sm ? base + sizeof(float) * (size_t)K * K : base;
-  MC_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(220 * 1024)));
+  smem_attr(chol_inv_kernel, (int)(220 * 1024));
   const int threads = K <= 128 ? 256 : 1024;
   chol_inv_kernel<<<1, threads, need, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, x_sm ? 1 : 0);
   MC_CHECK_LAUNCH();
@@ -1480,7 +1477,7 @@ bool orth_narrow(cudaStream_t st, int64_t R, int K, float *X, int ldx, const flo
   const bool small = K <= 16;
   const void *fn = small ? reinterpret_cast<const void *>(orth_narrow_kernel<16>)
                          : reinterpret_cast<const void *>(orth_narrow_kernel<32>);
-  MC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  smem_attr(fn, 220 * 1024);
   // CTAs: one to four per SM, at least 32 rows each, the rows and the
   // panel slices of a CTA in at most 220 KB / CTAs-per-SM of shared memory
   // (MC_ORTH_PER_SM caps the CTAs per SM)

@@ -1706,8 +1706,8 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   const EigPlan pl = eig_plan(K, kw);
   MC_REQUIRE(pl.vec_smem <= EIG_SMEM && pl.tri_smem <= EIG_SMEM, "eig_topk: shared-memory plan does not fit");
   float *gw = static_cast<float *>(work);
-  MC_CUDA(cudaFuncSetAttribute(eig_vectors_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
-  MC_CUDA(cudaFuncSetAttribute(eig_vectors_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+  smem_attr(eig_vectors_kernel<256>, (int)EIG_SMEM);
+  smem_attr(eig_vectors_kernel<1024>, (int)EIG_SMEM);
   const TriCfg tc = tri_cfg(K);
   bool done = false;
   if (pl.coop) {
@@ -1740,18 +1740,17 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
                                                      gw + pl.g_hv);
   } else if (K <= TM_K) {
     const size_t smem = sizeof(float) * ((size_t)K * (K + 1) / 2);
-    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(float) * (TM_K * (TM_K + 1) / 2))));
+    smem_attr(eig_tridiag_mid_kernel, (int)(sizeof(float) * (TM_K * (TM_K + 1) / 2)));
     eig_tridiag_mid_kernel<<<1, TM_THREADS, smem, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                         gw + pl.g_hv);
   } else if (tc.ppr == 8) {
-    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+    smem_attr(eig_tridiag_kernel<8, 1024>, (int)EIG_SMEM);
     eig_tridiag_kernel<8, 1024><<<1, 1024, pl.tri_smem, st>>>(MC_TRI_ARGS);
   } else if (tc.ppr == 16) {
-    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<16, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+    smem_attr(eig_tridiag_kernel<16, 1024>, (int)EIG_SMEM);
     eig_tridiag_kernel<16, 1024><<<1, 1024, pl.tri_smem, st>>>(MC_TRI_ARGS);
   } else {
-    MC_CUDA(cudaFuncSetAttribute(eig_tridiag_kernel<32, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM));
+    smem_attr(eig_tridiag_kernel<32, 512>, (int)EIG_SMEM);
     eig_tridiag_kernel<32, 512><<<1, 512, pl.tri_smem, st>>>(MC_TRI_ARGS);
   }
 #undef MC_TRI_ARGS
@@ -1761,11 +1760,11 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
     eig_bisect_kernel<<<kw, 32, 0, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam);
     MC_CHECK_LAUNCH();
     const size_t ism = sizeof(float) * 7 * (size_t)K;
-    MC_CUDA(cudaFuncSetAttribute(eig_invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(7 * 4 * 1024)));
+    smem_attr(eig_invit_kernel, (int)(7 * 4 * 1024));
     eig_invit_kernel<<<kw, 32, ism, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam, Zg, pl.vl.ldz);
     MC_CHECK_LAUNCH();
     const size_t osm = eig_orth_smem(K, kw);
-    MC_CUDA(cudaFuncSetAttribute(eig_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_orth_smem(TR_K, EO_KW)));
+    smem_attr(eig_orth_kernel, (int)eig_orth_smem(TR_K, EO_KW));
     eig_orth_kernel<<<1, EO_THREADS, osm, st>>>(K, kw, Zg, pl.vl.ldz);
     MC_CHECK_LAUNCH();
     eig_backtr_warp_kernel<<<(kw + BW_THREADS / 32 - 1) / (BW_THREADS / 32), BW_THREADS, 0, st>>>(
@@ -1791,7 +1790,7 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
                                                          gw + pl.g_hv, lam, W, ld_w, gw, pl.vl, ST_BISECT);
   MC_CHECK_LAUNCH();
   const size_t ism = sizeof(float) * 7 * (size_t)K;
-  MC_CUDA(cudaFuncSetAttribute(eig_invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(7 * 4 * 1024)));
+  smem_attr(eig_invit_kernel, (int)(7 * 4 * 1024));
   eig_invit_kernel<<<kw, 32, ism, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam, Zg, pl.vl.ldz);
   MC_CHECK_LAUNCH();
   eig_vectors_kernel<1024><<<1, 1024, pl.vec_smem, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,

@@ -1131,8 +1131,7 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
   }
   const int64_t ntiles = (R + NT_BM - 1) / NT_BM;
   const int grid = static_cast<int>(std::min<int64_t>(ntiles, sms));
-  MC_CUDA(cudaFuncSetAttribute(gemm_nn_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)NT_SMEM_LIMIT));
+  smem_attr(gemm_nn_tc_ws_kernel, (int)NT_SMEM_LIMIT);
   const int cat = p.Np <= 128 && use_nn_cat() ? 1 : 0;
   uint32_t cols = p.cols;
   while (cat && cols < static_cast<uint32_t>(4 * p.Np)) cols <<= 1;
@@ -1226,7 +1225,7 @@ void gemm_tn_tc(cudaStream_t st, int64_t R, int K1, int K2, const float *X1, int
   const TtPlan p = tt_plan(R, K1, K2, same);
   const CUtensorMap amap = tt_map(X1, R, K1, ld1, TT_KT * p.nsub);
   const CUtensorMap bmap = same ? amap : tt_map(X2, R, K2, ld2, TT_KT * p.nsub);
-  MC_CUDA(cudaFuncSetAttribute(gemm_tn_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM));
+  smem_attr(gemm_tn_tc_ws_kernel, (int)TT_SMEM);
   // the Gram of 33..64 columns in one MMA per step (hi^T [hi | lo])
   const bool sym = same && p.nbA == 2 && p.mt == 1 && use_tn_sym();
   gemm_tn_tc_ws_kernel<<<p.nsplit, TT_THREADS, p.smem, st>>>(amap, bmap, same ? 1 : 0, sym ? 1 : 0, R, p.nbA, p.nbB,
@@ -1266,7 +1265,7 @@ void gram_tc(cudaStream_t st, int64_t R, int K, const float *X, int ld, float *G
   const int nsplit = tc_nsplit(R);
   const int64_t rows_per = round_up((R + nsplit - 1) / nsplit, TC_KT);
   const size_t smem = TcSmem::total;
-  MC_CUDA(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  smem_attr(gram_tc_kernel, (int)smem);
   gram_tc_kernel<<<nsplit, TC_THREADS, smem, st>>>(map, R, K, nbox, two ? 1 : 0, N0, cols, rows_per, partial, Kp, err);
   MC_CHECK_LAUNCH();
   const int64_t total = (int64_t)K * K;

@@ -210,6 +210,22 @@ void copy_out_2d(cudaStream_t st, float *dst, int dst_cols, const float *src, in
 
 void sync(mc_handle h) { MC_CUDA(cudaStreamSynchronize(h->stream)); }
 
+}  // namespace
+
+void mc::smem_attr(const void *fn, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::tuple<const void *, int, int>> done;  // (kernel, device, bytes)
+  int dev = 0;
+  MC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  for (const auto &d : done)
+    if (std::get<0>(d) == fn && std::get<1>(d) == dev && std::get<2>(d) >= bytes) return;
+  MC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.emplace_back(fn, dev, bytes);
+}
+
+namespace {
+
 // count floats from host memory to dst (device) on the handle's stream,
 // through a pinned slot: returns without waiting for the copy; a slot is
 // rewritten only after its previous copy has run

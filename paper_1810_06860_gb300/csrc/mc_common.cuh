@@ -267,6 +267,15 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
               void *work);
 
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for a kernel once per
+// device and size (the launch paths call it before every launch; the driver
+// call is not free on a path of a hundred launches per iteration).
+void smem_attr(const void *fn, int bytes);
+template <typename F>
+inline void smem_attr(F *fn, int bytes) {
+  smem_attr(reinterpret_cast<const void *>(fn), bytes);
+}
+
 // Blocked right-looking Cholesky of the lower triangle of a 64 x 64 matrix in
 // shared memory (As[a][b], b <= a; 256 threads, all of which call it).  Every
 // entry takes its updates one fused multiply-add at a time in pivot order,
