@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(256)
 gemm_tn_reduce_kernel(int K1, int K2, int nsplit, const float *__restrict__ partial, int K1p, int K2p, bool sym,
                       int mirror, float *__restrict__ C, int ld_c, const int *__restrict__ skip = nullptr) {
   __shared__ float sh[8][33];
+  pdl_wait();
+  pdl_trigger();
   if (skip && *skip) return;
   const int64_t total = (int64_t)K1 * K2;
   const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
@@ -604,6 +606,8 @@ chol_inv_blk_kernel(int K, const float *__restrict__ G, int ld, float shift_rel,
   __shared__ float invd[CB_K], flags[CB_K], diagv[CB_K];
   __shared__ float s_tr, s_max;
   __shared__ unsigned s_dev;
+  pdl_wait();
+  pdl_trigger();
   if (skip_if && *skip_if) return;  // a pass the previous one made unnecessary
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const unsigned full = 0xffffffffu;
@@ -1277,7 +1281,8 @@ void gemm_tn_reduce_partials(cudaStream_t st, int K1, int K2, int nsplit, const 
                              float *C, int ld_c, const int *skip) {
   const int64_t total = (int64_t)K1 * K2;
   const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
-  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, nsplit, partial, K1p, K2p, false, 4, C, ld_c, skip);
+  launch_pdl(gemm_tn_reduce_kernel, dim3(nb), dim3(256), 0, st, K1, K2, nsplit, static_cast<const float *>(partial), K1p,
+             K2p, false, 4, C, ld_c, skip);
   MC_CHECK_LAUNCH();
 }
 
@@ -1318,7 +1323,8 @@ void gemm_tn_simt(cudaStream_t st, int64_t R, int K1, int K2, const float *X, in
   else launch_tn_small<64>(st, R, K1, K2, X, ld_x, Y, ld_y, symg, same, partial, pl, skip);
   const int64_t total = (int64_t)K1 * K2;
   const int nb = static_cast<int>(std::min<int64_t>((total + 31) / 32, 152 * 8));
-  gemm_tn_reduce_kernel<<<nb, 256, 0, st>>>(K1, K2, pl.nsplit, partial, pl.K1p, pl.K2p, symg, 4, C, ld_c, skip);
+  launch_pdl(gemm_tn_reduce_kernel, dim3(nb), dim3(256), 0, st, K1, K2, pl.nsplit, static_cast<const float *>(partial),
+             pl.K1p, pl.K2p, symg, 4, C, ld_c, skip);
   MC_CHECK_LAUNCH();
 }
 
@@ -1411,8 +1417,8 @@ void chol_inv(cudaStream_t st, int K, const float *G, int ld, float shift_rel, c
               float *Rinv, const int *skip_if, int *set_skip) {
   MC_REQUIRE(K >= 1 && K <= 1024, "chol_inv: K out of range");
   if (K <= CB_K && use_chol_blk()) {
-    chol_inv_blk_kernel<<<1, CB_THREADS, 0, st>>>(K, G, ld, shift_rel, ref_diag, ref_tol, Rinv, skip_if, set_skip,
-                                                  skip3_tol());
+    launch_pdl(chol_inv_blk_kernel, dim3(1), dim3(CB_THREADS), 0, st, K, G, ld, shift_rel, ref_diag, ref_tol, Rinv,
+               skip_if, set_skip, skip3_tol());
     MC_CHECK_LAUNCH();
     return;
   }

@@ -419,6 +419,8 @@ gemm_nn_tc_ws_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_cons
   __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int s_fail;
+  pdl_wait();
+  pdl_trigger();
   if (copy_if && *copy_if) {
     // copy mode (the factor is the identity): Z = X, K == N
     for (int64_t e = blockIdx.x * (int64_t)NW_THREADS + threadIdx.x; e < R * K; e += (int64_t)gridDim.x * NW_THREADS) {
@@ -770,6 +772,8 @@ gemm_tn_tc_ws_kernel(const __grid_constant__ CUtensorMap amap, const __grid_cons
   __shared__ __align__(8) uint64_t acc_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int s_fail;
+  pdl_wait();
+  pdl_trigger();
   if (skip && *skip) return;  // a pass the previous one made unnecessary
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tt_raw_smem) + 1023) & ~uintptr_t(1023));
   const int nbr = nbA + (same ? 0 : nbB);                  // raw boxes per stage
@@ -1135,9 +1139,8 @@ void gemm_nn_tc(cudaStream_t st, int64_t R, int K, int N, const float *X, int ld
   const int cat = p.Np <= 128 && use_nn_cat() ? 1 : 0;
   uint32_t cols = p.cols;
   while (cat && cols < static_cast<uint32_t>(4 * p.Np)) cols <<= 1;
-  gemm_nn_tc_ws_kernel<<<grid, NW_THREADS, p.smem, st>>>(map, zmap, zmode, p.ebuf, cat, R, K, N, p.Kp, p.Np, cols,
-                                                          p.nst, W, ld_w, colscale, alpha, beta, Z, ld_z, err,
-                                                          copy_if, ld_x, X);
+  launch_pdl(gemm_nn_tc_ws_kernel, dim3(grid), dim3(NW_THREADS), p.smem, st, map, zmap, zmode, p.ebuf, cat, R, K, N,
+             p.Kp, p.Np, cols, p.nst, W, ld_w, colscale, alpha, beta, Z, ld_z, err, copy_if, ld_x, X);
   MC_CHECK_LAUNCH();
 }
 
@@ -1228,9 +1231,9 @@ void gemm_tn_tc(cudaStream_t st, int64_t R, int K1, int K2, const float *X1, int
   smem_attr(gemm_tn_tc_ws_kernel, (int)TT_SMEM);
   // the Gram of 33..64 columns in one MMA per step (hi^T [hi | lo])
   const bool sym = same && p.nbA == 2 && p.mt == 1 && use_tn_sym();
-  gemm_tn_tc_ws_kernel<<<p.nsplit, TT_THREADS, p.smem, st>>>(amap, bmap, same ? 1 : 0, sym ? 1 : 0, R, p.nbA, p.nbB,
-                                                              p.Np, p.mt, sym ? 128u : p.cols, p.nsub, p.nr, p.ns,
-                                                              p.rows_per, partial, p.K1p, p.K2p, err, skip);
+  launch_pdl(gemm_tn_tc_ws_kernel, dim3(p.nsplit), dim3(TT_THREADS), p.smem, st, amap, bmap, same ? 1 : 0,
+             sym ? 1 : 0, R, p.nbA, p.nbB, p.Np, p.mt, sym ? 128u : p.cols, p.nsub, p.nr, p.ns, p.rows_per, partial,
+             p.K1p, p.K2p, err, skip);
   MC_CHECK_LAUNCH();
   gemm_tn_reduce_partials(st, K1, K2, p.nsplit, partial, p.K1p, p.K2p, C, ld_c, skip);
 }

@@ -212,6 +212,14 @@ void sync(mc_handle h) { MC_CUDA(cudaStreamSynchronize(h->stream)); }
 
 }  // namespace
 
+bool mc::use_pdl() {
+  static const bool on = [] {
+    const char *v = std::getenv("MC_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 void mc::smem_attr(const void *fn, int bytes) {
   static std::mutex mu;
   static std::vector<std::tuple<const void *, int, int>> done;  // (kernel, device, bytes)

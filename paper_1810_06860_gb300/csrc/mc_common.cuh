@@ -267,6 +267,34 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
               void *work);
 
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the previous kernel on the stream is finishing, so its
+// launch overlaps that kernel's tail; it calls pdl_wait() before anything
+// else, which returns once the previous kernel has completed and its writes
+// are visible (for an ordinary launch it returns at once).  MC_PDL=0 turns
+// the overlap off.
+bool use_pdl();
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the next kernel on the stream (if launched with launch_pdl) be
+// scheduled now; it still waits in pdl_wait() for this kernel's completion
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  static_assert(sizeof...(KArgs) == sizeof...(Args), "launch_pdl: every kernel argument is passed");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = use_pdl() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MC_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for a kernel once per
 // device and size (the launch paths call it before every launch; the driver
 // call is not free on a path of a hundred launches per iteration).
