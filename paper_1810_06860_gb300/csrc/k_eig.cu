@@ -346,6 +346,8 @@ __device__ __forceinline__ void tr_col(const float (&x)[TR_A][TR_B], float (&col
 __global__ void __launch_bounds__(TR_THREADS, 1)
 eig_tridiag_reg_kernel(int K, const float *__restrict__ A, int lda, float *__restrict__ g_d,
                        float *__restrict__ g_e, float *__restrict__ g_beta, float *__restrict__ Hv) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float vs[2][TR_K], ps[2][TR_K], colp[TR_K];
   __shared__ float part[TR_NW][TR_K];
   __shared__ float dotp[2][TR_K / 32];
@@ -1238,6 +1240,8 @@ eig_vectors_kernel(int K, int kw, const float *__restrict__ g_d, const float *__
 __global__ void __launch_bounds__(32)
 eig_invit_kernel(int K, int kw, const float *__restrict__ g_d, const float *__restrict__ g_e,
                  const float *__restrict__ lam_g, float *__restrict__ Z, int ldz) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) float ism[];
   float *d = ism, *e = d + K, *fa = e + K, *fb = fa + K, *fc = fb + K, *fl = fc + K, *z = fl + K;
   const int lane = threadIdx.x, t = blockIdx.x;
@@ -1376,6 +1380,8 @@ eig_backtr_kernel(int K, const float *__restrict__ g_beta, const float *__restri
 __global__ void __launch_bounds__(32)
 eig_bisect_kernel(int K, int kw, const float *__restrict__ g_d, const float *__restrict__ g_e,
                   float *__restrict__ lam_out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float d[TR_K], e2[TR_K];
   const int lane = threadIdx.x, t = blockIdx.x;
   const unsigned full = 0xffffffffu;
@@ -1434,6 +1440,8 @@ eig_bisect_kernel(int K, int kw, const float *__restrict__ g_d, const float *__r
 constexpr int EO_THREADS = 256, EO_KW = 64;
 __global__ void __launch_bounds__(EO_THREADS, 1)
 eig_orth_kernel(int K, int kw, float *__restrict__ Z, int ldz) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) float eo[];
   const int lz = kw | 1;                       // odd row stride
   float *Zs = eo;                              // K x lz
@@ -1547,6 +1555,8 @@ constexpr int BW_THREADS = 256, BW_CHUNK = 16;
 __global__ void __launch_bounds__(BW_THREADS)
 eig_backtr_warp_kernel(int K, int kw, const float *__restrict__ g_beta, const float *__restrict__ Hv,
                        const float *__restrict__ Z, int ldz, float *__restrict__ W, int ld_w) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ __align__(16) float hv[BW_CHUNK][TR_K];
   __shared__ float bt[BW_CHUNK];
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -1736,8 +1746,8 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
     eig_tridiag_small_kernel<<<1, TS_THREADS, 0, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
                                                        gw + pl.g_hv);
   } else if (K <= TR_K && tri_reg_on()) {
-    eig_tridiag_reg_kernel<<<1, TR_THREADS, 0, st>>>(K, A, lda, gw + pl.g_d, gw + pl.g_e, gw + pl.g_beta,
-                                                     gw + pl.g_hv);
+    launch_pdl(eig_tridiag_reg_kernel, dim3(1), dim3(TR_THREADS), 0, st, K, A, lda, gw + pl.g_d, gw + pl.g_e,
+               gw + pl.g_beta, gw + pl.g_hv);
   } else if (K <= TM_K) {
     const size_t smem = sizeof(float) * ((size_t)K * (K + 1) / 2);
     smem_attr(eig_tridiag_mid_kernel, (int)(sizeof(float) * (TM_K * (TM_K + 1) / 2)));
@@ -1757,18 +1767,18 @@ void eig_topk(cudaStream_t st, int K, int kw, const float *A, int lda, float *la
   MC_CHECK_LAUNCH();
   if (eig_many_cta(K, kw)) {
     float *Zg = gw + pl.vl.g_z;
-    eig_bisect_kernel<<<kw, 32, 0, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam);
+    launch_pdl(eig_bisect_kernel, dim3(kw), dim3(32), 0, st, K, kw, gw + pl.g_d, gw + pl.g_e, lam);
     MC_CHECK_LAUNCH();
     const size_t ism = sizeof(float) * 7 * (size_t)K;
     smem_attr(eig_invit_kernel, (int)(7 * 4 * 1024));
-    eig_invit_kernel<<<kw, 32, ism, st>>>(K, kw, gw + pl.g_d, gw + pl.g_e, lam, Zg, pl.vl.ldz);
+    launch_pdl(eig_invit_kernel, dim3(kw), dim3(32), ism, st, K, kw, gw + pl.g_d, gw + pl.g_e, lam, Zg, pl.vl.ldz);
     MC_CHECK_LAUNCH();
     const size_t osm = eig_orth_smem(K, kw);
     smem_attr(eig_orth_kernel, (int)eig_orth_smem(TR_K, EO_KW));
-    eig_orth_kernel<<<1, EO_THREADS, osm, st>>>(K, kw, Zg, pl.vl.ldz);
+    launch_pdl(eig_orth_kernel, dim3(1), dim3(EO_THREADS), osm, st, K, kw, Zg, pl.vl.ldz);
     MC_CHECK_LAUNCH();
-    eig_backtr_warp_kernel<<<(kw + BW_THREADS / 32 - 1) / (BW_THREADS / 32), BW_THREADS, 0, st>>>(
-        K, kw, gw + pl.g_beta, gw + pl.g_hv, Zg, pl.vl.ldz, W, ld_w);
+    launch_pdl(eig_backtr_warp_kernel, dim3((kw + BW_THREADS / 32 - 1) / (BW_THREADS / 32)), dim3(BW_THREADS), 0, st, K,
+               kw, gw + pl.g_beta, gw + pl.g_hv, Zg, pl.vl.ldz, W, ld_w);
     MC_CHECK_LAUNCH();
     return;
   }

@@ -256,6 +256,8 @@ __global__ void __launch_bounds__(256)
 spmm_seg_kernel(int64_t nseg, const int4 *__restrict__ segs, const int *__restrict__ idx,
                 const float *__restrict__ val, const float *__restrict__ X, int ld_x, int K4,
                 float *__restrict__ out, int ld_out, float *__restrict__ partial) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int L = 32 / G;  // lanes per group
   const int lane = threadIdx.x & 31;
   const int64_t seg = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -384,6 +386,8 @@ __global__ void to_bf16_kernel(int64_t rows, int cols, const float *__restrict__
 __global__ void spmm_fixup_kernel(int64_t nsplit, const int *__restrict__ split_row,
                                   const int *__restrict__ split_slot, const float *__restrict__ partial, int K,
                                   float *__restrict__ out, int ld_out) {
+  pdl_wait();
+  pdl_trigger();
   const int K4 = K / 4;
   const int lane = threadIdx.x & 31;
   const int64_t nw = nsplit * K4;
@@ -430,6 +434,8 @@ template <int KM4>
 __global__ void spmm_fixup_rows_kernel(int64_t nsplit, const int *__restrict__ split_row,
                                        const int *__restrict__ split_slot, const float *__restrict__ partial, int K,
                                        float *__restrict__ out, int ld_out, int nchunk) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wi < nsplit * nchunk; wi += wstride) {
@@ -506,6 +512,8 @@ sddmm_update_kernel(int64_t nnz, const int *__restrict__ rix, const int *__restr
                     const float *__restrict__ mval, float *__restrict__ y, const float *__restrict__ Us, int ld_us,
                     const float *__restrict__ V, int ld_v, int r4, float delta, int update,
                     double *__restrict__ block_sq, float *__restrict__ x_out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float wsum[kSddmmThreads / 32];
   float sq = 0.f;
   for (int64_t e = blockIdx.x * (int64_t)kSddmmThreads + threadIdx.x; e < nnz;
@@ -743,9 +751,9 @@ template <int G>
 void launch_seg(int u, int64_t blocks, int threads, cudaStream_t st, int64_t nseg, const int4 *segs, const int *idx,
                 const float *val, const float *X, int ld_x, int K4, float *out, int ld_out, float *partial) {
 #define MC_SPMM_ARGS nseg, segs, idx, val, X, ld_x, K4, out, ld_out, partial
-  if (u >= 4 && G * 4 <= 32) spmm_seg_kernel<G, (G * 4 <= 32 ? 4 : 1)><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else if (u >= 2 && G * 2 <= 32) spmm_seg_kernel<G, (G * 2 <= 32 ? 2 : 1)><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
-  else spmm_seg_kernel<G, 1><<<blocks, threads, 0, st>>>(MC_SPMM_ARGS);
+  if (u >= 4 && G * 4 <= 32) launch_pdl(spmm_seg_kernel<G, (G * 4 <= 32 ? 4 : 1)>, dim3(blocks), dim3(threads), 0, st, MC_SPMM_ARGS);
+  else if (u >= 2 && G * 2 <= 32) launch_pdl(spmm_seg_kernel<G, (G * 2 <= 32 ? 2 : 1)>, dim3(blocks), dim3(threads), 0, st, MC_SPMM_ARGS);
+  else launch_pdl(spmm_seg_kernel<G, 1>, dim3(blocks), dim3(threads), 0, st, MC_SPMM_ARGS);
 #undef MC_SPMM_ARGS
 }
 }  // namespace
@@ -765,15 +773,15 @@ static void launch_fixup(cudaStream_t st, const SegPlan &plan, const float *part
   const int K4 = K / 4;
   const int *sr = plan.split_row.as<int>(), *ss = plan.split_slot.as<int>();
   if (K4 <= 4) {
-    spmm_fixup_rows_kernel<4><<<grid_for(plan.nsplit * 32, 256, 1 << 20), 256, 0, st>>>(plan.nsplit, sr, ss, partial,
-                                                                                       K, out, ld_out, 1);
+    launch_pdl(spmm_fixup_rows_kernel<4>, dim3(grid_for(plan.nsplit * 32, 256, 1 << 20)), dim3(256), 0, st,
+               plan.nsplit, sr, ss, partial, K, out, ld_out, 1);
   } else if (K4 <= 64 && use_fixup_rows()) {
     const int nchunk = (K4 + 7) / 8;
-    spmm_fixup_rows_kernel<8><<<grid_for(plan.nsplit * nchunk * 32, 256, 1 << 20), 256, 0, st>>>(
-        plan.nsplit, sr, ss, partial, K, out, ld_out, nchunk);
+    launch_pdl(spmm_fixup_rows_kernel<8>, dim3(grid_for(plan.nsplit * nchunk * 32, 256, 1 << 20)), dim3(256), 0, st,
+               plan.nsplit, sr, ss, partial, K, out, ld_out, nchunk);
   } else {
-    spmm_fixup_kernel<<<grid_for(plan.nsplit * K4 * 32, 256), 256, 0, st>>>(plan.nsplit, sr, ss, partial, K, out,
-                                                                           ld_out);
+    launch_pdl(spmm_fixup_kernel, dim3(grid_for(plan.nsplit * K4 * 32, 256)), dim3(256), 0, st, plan.nsplit, sr, ss,
+               partial, K, out, ld_out);
   }
   MC_CHECK_LAUNCH();
 }
@@ -911,8 +919,8 @@ int sddmm_update(cudaStream_t st, int64_t nnz, const int *rix, const int *col, c
   MC_REQUIRE(r >= 0, "sddmm: negative rank");
   MC_REQUIRE(ld_us % 4 == 0 && ld_v % 4 == 0 && ld_us >= r && ld_v >= r, "sddmm: bad leading dims");
   const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSddmmBlocks, (nnz + kSddmmThreads - 1) / kSddmmThreads)));
-  sddmm_update_kernel<<<nb, kSddmmThreads, 0, st>>>(nnz, rix, col, mval, y, Us, ld_us, V, ld_v, (r + 3) / 4, delta,
-                                                     update, block_sq, x_out);
+  launch_pdl(sddmm_update_kernel, dim3(nb), dim3(kSddmmThreads), 0, st, nnz, rix, col, mval, y, Us, ld_us, V, ld_v,
+             (r + 3) / 4, delta, update, block_sq, x_out);
   MC_CHECK_LAUNCH();
   return nb;
 }
