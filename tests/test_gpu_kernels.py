@@ -215,6 +215,49 @@ def test_spmm_launch_shapes_bit_identical(mc, tmp_path):
             assert np.array_equal(a, b)
 
 
+_PDL_PROBE = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import mc_synth, paper_1810_06860_gb300 as mc
+o = mc_synth.ratings(m=6000, n=2000, N=240000, seed=5)
+prm = mc.params(tau=5.0 * np.sqrt(o.m * o.n), delta=1.9, eps=1e-6, recycle=3, seed=1)
+out = []
+with mc.Handle.from_observed(o) as h:
+    for _ in range(6):
+        h.svt_step(prm)
+    out.append(h.get_values())
+    s, U, V = h.rsvd_bki(50, s=10, p=3, seed=3)
+    out += [s, U, V]
+np.savez({path!r}, *out)
+"""
+
+
+def test_dependent_launches_bit_identical(mc, tmp_path):
+    """Programmatic dependent launches (each kernel waits for its predecessor
+    in griddepcontrol.wait) give the same bits as ordinary launches: six SVT
+    iterations and an rSVD-BKI at k = 50 (60-column blocks through the
+    tensor-core Gram and product, the blocked Cholesky, the SpMM and the
+    eigensolver chain), run with MC_PDL unset and with MC_PDL=0."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = []
+    for flag in (None, "0"):
+        path = str(tmp_path / f"p{len(res)}.npz")
+        env = dict(os.environ)
+        env.pop("MC_PDL", None)
+        if flag is not None:
+            env["MC_PDL"] = flag
+        subprocess.run([sys.executable, "-c", _PDL_PROBE.format(root=root, path=path)], env=env, check=True,
+                       timeout=600)
+        z = np.load(path)
+        res.append([z[f"arr_{i}"] for i in range(len(z.files))])
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
 def test_coo_ingest_matches_csr(mc):
     """Coordinates in a shuffled order give the same iterate, bit for bit, as
     the CSR ingest; a repeated pair and an index out of range are refused."""
